@@ -1,0 +1,328 @@
+"""Seeded synthetic rating matrices shaped like the paper's workloads.
+
+This module only produces inputs: sparse rating triples (row, col, value), a
+held-out test split and the model settings that go with them.  It holds none of
+the sampler's arithmetic, and both the CUDA path and the CPU oracle consume
+what it returns.
+
+All randomness is drawn with numpy's PCG64 from the given seed, so a dataset is
+fixed by (recipe, seed).  The deterministic bulk transforms (inverse-CDF index
+lookup, de-duplication, planted dot products in float64) run in torch on the
+requested device only to make the 100M-entry recipes take seconds instead of
+minutes; they are exact integer operations or float64 sums, so a CPU and a GPU
+run give the same triples up to float64 rounding of the planted values.
+
+Recipes (paper Sec. V-B names the public datasets; only their shapes are used):
+
+* ``tiny``: planted U (1000x10), V (500x10) with entries of std 1/sqrt(10),
+  20k distinct cells uniformly at random, value = u.v + N(0, 0.5^2).
+* ``tiny_dense``: same sizes, 40% density, entry std (1/K)^(1/4) so that u.v has
+  unit variance, noise std 0.5.
+* ``movielens``: 138,493 x 26,744, 20M cells, Zipf(1.1) row and column weights
+  (Chung-Lu pairs, degrees capped by the opposite side), value =
+  round-to-half(3.5 + u.v + N(0, 0.8^2)) clipped to [0.5, 5], planted rank 32.
+* ``chembl``: 480,000 x 5,800, 1.0M cells, uniform row weights, power-law
+  column weights chosen so the top 10% of columns hold about 72% of the cells,
+  value = 6 + 1.118 u.v + N(0, 1), planted rank 64 with unit-variance u.v.
+* ``netflix``: 480,189 x 17,770, 100M cells, power-law weights on both sides
+  (largest expected column degree 230k, largest expected row degree 8,885),
+  value = clip(round(3.6 + u.v + N(0, 1)), 1, 5), planted rank 100.
+* ``powerlaw``: the same Chung-Lu construction at any size (parity cases).
+
+Every recipe holds out 10% of the cells, chosen uniformly, as the test set.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+__all__ = ["Dataset", "tiny", "tiny_dense", "movielens", "chembl", "netflix",
+           "powerlaw", "uniform", "make", "RECIPES"]
+
+
+@dataclasses.dataclass
+class Dataset:
+    name: str
+    M: int                 # rows (users / compounds)
+    N: int                 # columns (movies / targets)
+    K: int                 # latent dimension used to fit it
+    alpha: float           # observation precision used to fit it
+    train_row: np.ndarray  # int32 [nnz_train]
+    train_col: np.ndarray  # int32 [nnz_train]
+    train_val: np.ndarray  # float32 [nnz_train]
+    test_row: np.ndarray   # int32 [nnz_test]
+    test_col: np.ndarray   # int32 [nnz_test]
+    test_val: np.ndarray   # float32 [nnz_test]
+    clip: tuple | None = None   # rating range used to clip predictions, if any
+    note: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.train_row.shape[0])
+
+    def prior(self):
+        """Hyperprior of the recipes: mu0 = 0, beta0 = 2, nu0 = K, W0 = I."""
+        K = self.K
+        return dict(mu0=np.zeros(K), beta0=2.0, nu0=float(K), W0=np.eye(K))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _split(rng, rows, cols, vals, frac=0.1):
+    n = rows.shape[0]
+    perm = rng.permutation(n)
+    nt = int(round(frac * n))
+    te, tr = perm[:nt], perm[nt:]
+    return (rows[tr], cols[tr], vals[tr], rows[te], cols[te], vals[te])
+
+
+def _planted_dot(U, V, r, c, device):
+    """u_r . v_c in float64 for every pair, in chunks on ``device``."""
+    torch = _torch()
+    Ut = torch.from_numpy(U).to(device)
+    Vt = torch.from_numpy(V).to(device)
+    rt = torch.from_numpy(r.astype(np.int64))
+    ct = torch.from_numpy(c.astype(np.int64))
+    out = np.empty(r.shape[0], np.float64)
+    step = 1 << 21
+    for s in range(0, r.shape[0], step):
+        a = Ut[rt[s:s + step].to(device)]
+        b = Vt[ct[s:s + step].to(device)]
+        out[s:s + step] = (a * b).sum(1).cpu().numpy()
+    return out
+
+
+def _weights_cdf(rng, n, expo):
+    """Power-law weights (rank+1)^-expo scattered over ids by a permutation."""
+    w = np.arange(1, n + 1, dtype=np.float64) ** (-expo)
+    ids = rng.permutation(n)
+    wid = np.empty(n, np.float64)
+    wid[ids] = w
+    cdf = np.cumsum(wid)
+    cdf /= cdf[-1]
+    cdf[-1] = 1.0
+    return wid / wid.sum(), cdf
+
+
+def _chung_lu(rng, M, N, nnz, row_cdf, col_cdf, device):
+    """Distinct (row, col) cells drawn i.i.d. from row x column weights.
+
+    Draw, drop duplicates, top up the deficit, repeat; then keep a uniformly
+    random subset of exactly ``nnz`` cells in random order.
+    """
+    torch = _torch()
+    rc = torch.from_numpy(row_cdf).to(device)
+    cc = torch.from_numpy(col_cdf).to(device)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    need = nnz
+    for _ in range(64):
+        draw = int(need * 1.08) + 1024
+        ur = torch.from_numpy(rng.random(draw)).to(device)
+        uc = torch.from_numpy(rng.random(draw)).to(device)
+        r = torch.searchsorted(rc, ur, right=True).clamp_(max=M - 1)
+        c = torch.searchsorted(cc, uc, right=True).clamp_(max=N - 1)
+        keys = torch.unique(torch.cat([keys, r * N + c]))
+        need = nnz - int(keys.numel())
+        if need <= 0:
+            break
+    else:
+        raise RuntimeError("Chung-Lu sampling did not reach the requested nnz")
+    keys = keys.cpu().numpy()
+    sel = rng.permutation(keys.shape[0])[:nnz]
+    keys = keys[sel]
+    return (keys // N).astype(np.int32), (keys % N).astype(np.int32)
+
+
+def _uniform_cells(rng, M, N, nnz):
+    """``nnz`` distinct cells uniformly at random, in random order."""
+    total = M * N
+    if nnz > total:
+        raise ValueError("more cells than the matrix holds")
+    if nnz * 4 > total:
+        keys = rng.permutation(total)[:nnz]
+    else:
+        keys = np.empty(0, np.int64)
+        while keys.shape[0] < nnz:
+            extra = rng.integers(0, total, size=int((nnz - keys.shape[0]) * 1.2) + 16)
+            keys = np.unique(np.concatenate([keys, extra]))
+        keys = keys[rng.permutation(keys.shape[0])[:nnz]]
+    return (keys // N).astype(np.int32), (keys % N).astype(np.int32)
+
+
+def _bisect_expo(n, target_share, lo=0.0, hi=3.0):
+    """Exponent s with max weight share 1/H(n, s) equal to ``target_share``."""
+    ranks = np.arange(1, n + 1, dtype=np.float64)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        w = ranks ** (-mid)
+        share = 1.0 / w.sum()
+        if share < target_share:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def _bisect_top_frac(n, frac_cols, target, lo=0.0, hi=3.0):
+    """Exponent s so the top ``frac_cols`` of weights hold ``target`` of the mass."""
+    ranks = np.arange(1, n + 1, dtype=np.float64)
+    top = max(1, int(round(frac_cols * n)))
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        w = ranks ** (-mid)
+        share = w[:top].sum() / w.sum()
+        if share < target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def tiny(seed: int = 0) -> Dataset:
+    rng = np.random.default_rng(seed)
+    M, N, K = 1000, 500, 10
+    U = rng.normal(0.0, 1.0 / math.sqrt(K), size=(M, K))
+    V = rng.normal(0.0, 1.0 / math.sqrt(K), size=(N, K))
+    r, c = _uniform_cells(rng, M, N, 20000)
+    val = np.einsum("ij,ij->i", U[r], V[c]) + rng.normal(0.0, 0.5, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32))
+    return Dataset("tiny", M, N, K, 4.0, *parts, note="planted rank 10, noise std 0.5")
+
+
+def tiny_dense(seed: int = 0) -> Dataset:
+    rng = np.random.default_rng(seed)
+    M, N, K = 1000, 500, 10
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    r, c = _uniform_cells(rng, M, N, int(0.4 * M * N))
+    val = np.einsum("ij,ij->i", U[r], V[c]) + rng.normal(0.0, 0.5, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32))
+    return Dataset("tiny_dense", M, N, K, 4.0, *parts,
+                   note="planted rank 10 with unit-variance signal, noise std 0.5")
+
+
+def uniform(M: int, N: int, nnz: int, K: int, seed: int = 0, alpha: float = 2.0,
+            noise: float = 0.5, test_frac: float = 0.1) -> Dataset:
+    """Uniformly placed cells with a planted unit-variance rank-K signal."""
+    rng = np.random.default_rng(seed)
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    r, c = _uniform_cells(rng, M, N, nnz)
+    val = np.einsum("ij,ij->i", U[r], V[c]) + rng.normal(0.0, noise, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32), test_frac)
+    return Dataset(f"uniform_{M}x{N}_{nnz}_K{K}", M, N, K, alpha, *parts)
+
+
+def powerlaw(M: int, N: int, nnz: int, K: int, row_expo: float, col_expo: float,
+             seed: int = 0, alpha: float = 2.0, noise: float = 1.0, offset: float = 0.0,
+             device: str = "cpu", name: str | None = None,
+             test_frac: float = 0.1) -> Dataset:
+    """Chung-Lu cells with power-law row/column weights and a planted signal."""
+    rng = np.random.default_rng(seed)
+    _, rcdf = _weights_cdf(rng, M, row_expo)
+    _, ccdf = _weights_cdf(rng, N, col_expo)
+    r, c = _chung_lu(rng, M, N, nnz, rcdf, ccdf, device)
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    val = offset + _planted_dot(U, V, r, c, device) + rng.normal(0.0, noise, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32), test_frac)
+    return Dataset(name or f"powerlaw_{M}x{N}_{nnz}_K{K}", M, N, K, alpha, *parts)
+
+
+def movielens(seed: int = 0, device: str = "cpu") -> Dataset:
+    rng = np.random.default_rng(seed)
+    M, N, K, nnz = 138_493, 26_744, 32, 20_000_000
+    _, rcdf = _weights_cdf(rng, M, 1.1)
+    _, ccdf = _weights_cdf(rng, N, 1.1)
+    r, c = _chung_lu(rng, M, N, nnz, rcdf, ccdf, device)
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    raw = 3.5 + _planted_dot(U, V, r, c, device) + rng.normal(0.0, 0.8, size=r.shape[0])
+    val = np.clip(np.round(raw * 2.0) / 2.0, 0.5, 5.0).astype(np.float32)
+    parts = _split(rng, r, c, val)
+    return Dataset("movielens", M, N, K, 1.0 / 0.8 ** 2, *parts, clip=(0.5, 5.0),
+                   note="ml-20m shape: Zipf(1.1) weights, half-star ratings")
+
+
+def chembl(seed: int = 0, device: str = "cpu") -> Dataset:
+    rng = np.random.default_rng(seed)
+    M, N, K, nnz = 480_000, 5_800, 64, 1_000_000
+    rcdf = np.arange(1, M + 1, dtype=np.float64) / M
+    rcdf[-1] = 1.0
+    expo = _bisect_top_frac(N, 0.10, 0.72)
+    _, ccdf = _weights_cdf(rng, N, expo)
+    r, c = _chung_lu(rng, M, N, nnz, rcdf, ccdf, device)
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    s = math.sqrt(1.5 ** 2 - 1.0)
+    val = 6.0 + s * _planted_dot(U, V, r, c, device) + rng.normal(0.0, 1.0, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32))
+    return Dataset("chembl", M, N, K, 1.0, *parts,
+                   note=f"ChEMBL IC50 shape: uniform rows, column exponent {expo:.3f}")
+
+
+def netflix(seed: int = 0, device: str = "cpu") -> Dataset:
+    rng = np.random.default_rng(seed)
+    M, N, K, nnz = 480_189, 17_770, 100, 100_000_000
+    col_expo = _bisect_expo(N, 230_000 / nnz)
+    row_expo = _bisect_expo(M, (N // 2) / nnz)
+    _, rcdf = _weights_cdf(rng, M, row_expo)
+    _, ccdf = _weights_cdf(rng, N, col_expo)
+    r, c = _chung_lu(rng, M, N, nnz, rcdf, ccdf, device)
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    raw = 3.6 + _planted_dot(U, V, r, c, device) + rng.normal(0.0, 1.0, size=r.shape[0])
+    val = np.clip(np.round(raw), 1.0, 5.0).astype(np.float32)
+    parts = _split(rng, r, c, val)
+    return Dataset("netflix", M, N, K, 2.0, *parts, clip=(1.0, 5.0),
+                   note=f"Netflix shape: row exponent {row_expo:.3f}, column exponent {col_expo:.3f}")
+
+
+RECIPES = {
+    "tiny": tiny,
+    "tiny_dense": tiny_dense,
+    "movielens": movielens,
+    "chembl": chembl,
+    "netflix": netflix,
+}
+
+
+def make(name: str, seed: int = 0, device: str = "cpu", cache_dir: str | None = None) -> Dataset:
+    """Build a named recipe, optionally caching it as .npz under ``cache_dir``."""
+    fn = RECIPES[name]
+    kwargs = {} if name.startswith("tiny") else {"device": device}
+    if cache_dir is None:
+        cache_dir = os.environ.get("BPMF_SYNTH_CACHE")
+    path = None
+    if cache_dir:
+        os.makedirs(cache_dir, exist_ok=True)
+        path = os.path.join(cache_dir, f"{name}_s{seed}_v1.npz")
+        if os.path.exists(path):
+            z = np.load(path, allow_pickle=False)
+            meta = z["meta"]
+            clip = None if np.isnan(meta[5]) else (float(meta[5]), float(meta[6]))
+            return Dataset(name, int(meta[0]), int(meta[1]), int(meta[2]), float(meta[3]),
+                           z["train_row"], z["train_col"], z["train_val"],
+                           z["test_row"], z["test_col"], z["test_val"], clip=clip)
+    ds = fn(seed, **kwargs)
+    if path:
+        clip = ds.clip or (float("nan"), float("nan"))
+        meta = np.array([ds.M, ds.N, ds.K, ds.alpha, 0.0, clip[0], clip[1]], np.float64)
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, meta=meta, train_row=ds.train_row, train_col=ds.train_col,
+                 train_val=ds.train_val, test_row=ds.test_row, test_col=ds.test_col,
+                 test_val=ds.test_val)
+        os.replace(tmp, path)
+    return ds
