@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput of the BPMF Gibbs sampler: rows sampled per second per iteration.
+
+One step is one Gibbs iteration of Algorithm 1 over the whole workload:
+hyperparameters of the users, every user row, hyperparameters of the movies,
+every movie row, then the test predictions and RMSE.  rows/s = (M + N) per
+iteration / iteration time.
+
+Default workload: Netflix-shaped synthetic ratings (480,189 x 17,770, 100M
+ratings, 10% held out, power-law degrees, K = 100), generated on the device
+from a seed.  The timed region starts with every input resident in HBM.  Its
+working set per iteration (two compressed copies of 90M ratings, 1.4 GB, plus
+the factors) is far larger than the 129 MB L2, so no flush is needed.
+
+Reported beside the main value: the plain FP32 GPU form on the same workload,
+an end-to-end number through the C ABI from pinned host buffers (bpmf_init,
+the iterations, copies of the result), the roofline of the dominant kernel,
+and the FP64 CPU oracle on a bounded sample of the workload.
+
+--impl reference runs the CPU oracle (the reference arm) on bounded samples.
+Multi-GPU (torchrun): every rank runs an independent replica; no collective
+touches the data path (rows of a job never leave their GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rows sampled/s per Gibbs sweep"
+UNIT = "rows/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="netflix")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ dist --
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ------------------------------------------------------------- workload --
+
+def load_workload(name, seed, device):
+    import synth
+    cache = os.environ.get("BPMF_SYNTH_CACHE", "/tmp/bpmf_synth_cache")
+    return synth.make(name, seed=seed, device=device, cache_dir=cache)
+
+
+def algorithmic_work(ds, K):
+    """Flops and bytes of one half-sweep per side (the unit counts of the row update)."""
+    nnz = ds.nnz
+    out = {}
+    for side, (R, C) in enumerate(((ds.M, ds.N), (ds.N, ds.M))):
+        flops = nnz * (K * (K + 1) + 2 * K) + R * (K ** 3 / 3 + 3 * K ** 2)
+        nbytes = nnz * 8 + C * 4 * K + R * (4 * K + 8)
+        out[side] = (flops, nbytes)
+    return out
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "of measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "of fallback"
+
+
+# ------------------------------------------------------------- GPU arms --
+
+def device_arm(bp, ds, path, steps, warmup, world, stream):
+    """Steady-state iterations with every input already in HBM."""
+    import torch
+    dev = torch.device("cuda")
+    t = {k: torch.from_numpy(getattr(ds, k)).to(dev) for k in
+         ("train_row", "train_col", "train_val", "test_row", "test_col", "test_val")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = bp.Sampler(ds.M, ds.N, t["train_row"], t["train_col"], t["train_val"], K=ds.K,
+                   alpha=ds.alpha, seed=0, path=path, stream=stream)
+    s.set_test(t["test_row"], t["test_col"], t["test_val"])
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        s.step()
+    s.set_timing(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        s.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / steps
+    phase_ms, phase_cnt, kernels = s.timing()
+    rmse = s.test_rmse()
+    info = [s.sweep_info(0), s.sweep_info(1)]
+    s.close()
+    del t
+    torch.cuda.empty_cache()
+    return dict(ms=ms, init_s=init_s, phase_ms=phase_ms, phase_cnt=phase_cnt, kernels=kernels,
+                rmse=rmse, info=info)
+
+
+def e2e_arm(bp, ds, path, steps, stream):
+    """A whole job through the C ABI from pinned host buffers: bpmf_init (H2D of
+    the ratings, structure build), bpmf_set_test, `steps` iterations, then the
+    factors and the RMSE back to the host."""
+    import torch
+    pin = {k: torch.from_numpy(getattr(ds, k)).pin_memory() for k in
+           ("train_row", "train_col", "train_val", "test_row", "test_col", "test_val")}
+    host = {k: v.numpy() for k, v in pin.items()}
+    U = torch.empty((ds.M, ds.K), dtype=torch.float32).pin_memory().numpy()
+    V = torch.empty((ds.N, ds.K), dtype=torch.float32).pin_memory().numpy()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s = bp.Sampler(ds.M, ds.N, host["train_row"], host["train_col"], host["train_val"], K=ds.K,
+                   alpha=ds.alpha, seed=1, path=path, stream=stream)
+    s.set_test(host["test_row"], host["test_col"], host["test_val"])
+    for _ in range(steps):
+        s.step()
+    s.get_state(U=U, V=V)
+    rmse = s.test_rmse()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s.close()
+    h2d = sum(host[k].nbytes for k in host)
+    d2h = U.nbytes + V.nbytes + 16
+    return dict(ms=ms, rmse=rmse, h2d=h2d / steps, d2h=d2h / steps)
+
+
+# ----------------------------------------------------------- CPU oracle --
+
+def cpu_oracle_rate(ds, K, budget_s, seed=0):
+    """Oracle rows/s on a bounded sample of one iteration of the workload.
+
+    The oracle's hyper draw runs on every row of each side; the row draws run
+    on uniform random samples of users and movies, sized to stay within the
+    budget; predictions on a sample of the test set.  Each part is scaled by
+    its sampling fraction to one full iteration."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    mu = oracle.mean(ds.train_val)
+    csr = oracle.build_compressed(ds.M, ds.train_row, ds.train_col, ds.train_val, mu)
+    csc = oracle.build_compressed(ds.N, ds.train_col, ds.train_row, ds.train_val, mu)
+    U = rng.normal(size=(ds.M, K)) * 0.3
+    V = rng.normal(size=(ds.N, K)) * 0.3
+    prior = dict(mu0=np.zeros(K), beta0=2.0, nu0=float(K), W0=np.eye(K))
+    parts = {}
+    t_iter = 0.0
+    rows_done = 0
+    for side, (X, Xo, (ptr, idx, val)) in enumerate(((U, V, csr), (V, U, csc))):
+        t0 = time.perf_counter()
+        Lam, m = oracle.sample_hyper(X, prior, 0, 0, side)
+        th = time.perf_counter() - t0
+        R = X.shape[0]
+        deg = np.diff(ptr)
+        avg_cost = float(np.mean(deg)) * K * K + K ** 3 / 3.0
+        # size the sample to about a third of the budget per side
+        n = 16
+        while True:
+            sub = rng.choice(R, size=min(n, R), replace=False)
+            Xs = X.copy() if side == 0 else X.copy()
+            t0 = time.perf_counter()
+            oracle.sweep(side, ptr, idx, val, Xo, Lam, m, ds.alpha, 0, 0, Xs, subset=sub)
+            ts = time.perf_counter() - t0
+            if ts > budget_s / 3 or n >= R:
+                break
+            n = int(min(R, n * max(2.0, 0.8 * (budget_s / 3) / max(ts, 1e-4))))
+        per_row = ts / len(sub)
+        parts[side] = dict(hyper_s=th, rows=len(sub), sweep_s=ts, est_sweep_s=per_row * R,
+                           sampled_mean_degree=float(np.mean(deg[sub])), mean_degree=float(np.mean(deg)))
+        t_iter += th + per_row * R
+        rows_done += len(sub)
+    nt = len(ds.test_row)
+    ns = min(nt, 1_000_000)
+    sel = rng.choice(nt, size=ns, replace=False)
+    t0 = time.perf_counter()
+    oracle.predict(ds.test_row[sel], ds.test_col[sel], U, V, mu)
+    tp = (time.perf_counter() - t0) * nt / ns
+    t_iter += tp
+    rate = (ds.M + ds.N) / t_iter
+    sample = (f"hyper draws on all rows; row draws on {parts[0]['rows']} random users and "
+              f"{parts[1]['rows']} random movies; predictions on {ns} test pairs; scaled to one "
+              f"iteration ({t_iter:.1f} s estimated)")
+    return rate, sample, oracle.max_threads(), parts
+
+
+# ----------------------------------------------------------------- main --
+
+def main():
+    args = parse()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    import torch
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+    import paper_1705_04159_gb300 as bp
+    bp.build()
+    bp.lib()
+    stream = torch.cuda.current_stream()
+    ds = load_workload(args.workload, args.seed, "cuda")
+    K = ds.K
+    work = algorithmic_work(ds, K)
+
+    with ClockSampler(local) as clk:
+        mixed = device_arm(bp, ds, bp.PATH_MIXED, args.steps, args.warmup, world, stream)
+    clocks = clk.summary()
+    ms = max_over_ranks(world, mixed["ms"])
+    rows = ds.M + ds.N
+    value = world * rows / (ms / 1e3)
+
+    plain = None
+    if not args.no_plain:
+        p = device_arm(bp, ds, bp.PATH_PLAIN, max(3, args.steps // 2), args.warmup, world, stream)
+        pm = max_over_ranks(world, p["ms"])
+        plain = {"value": world * rows / (pm / 1e3), "ms_per_step": pm,
+                 "rows_users_ms": p["phase_ms"]["rows_users"] / max(1, p["phase_cnt"]["rows_users"]),
+                 "rows_movies_ms": p["phase_ms"]["rows_movies"] / max(1, p["phase_cnt"]["rows_movies"]),
+                 "rmse_mean": p["rmse"][1]}
+
+    e2e = None
+    if not args.no_e2e:
+        e = e2e_arm(bp, ds, bp.PATH_MIXED, args.steps, stream)
+        em = max_over_ranks(world, e["ms"])
+        e2e = {"value": world * rows * args.steps / (em / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(e["h2d"]), "d2h_bytes_per_step": int(e["d2h"]),
+               "job_ms": em, "iterations": args.steps}
+
+    # dominant kernel: the row-update phase with the larger time per launch
+    ph, pc = mixed["phase_ms"], mixed["phase_cnt"]
+    per = {k: ph[k] / max(1, pc[k]) for k in ph}
+    dom = max(("rows_users", "rows_movies"), key=lambda k: per[k])
+    side = 0 if dom == "rows_users" else 1
+    flops, nbytes = work[side]
+    achieved = flops / (per[dom] / 1e3) / 1e12
+    roofline = {"kernel": f"row update, {'users' if side == 0 else 'movies'} side",
+                "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_note": "FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "ms_per_launch": per[dom]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, sample, cores, parts = cpu_oracle_rate(ds, K, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Netflix-shaped ratings generated on the device)",
+            "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train + "
+                                   f"{len(ds.test_row)} test ratings, K={K}",
+                       "path": "mixed", "global_batch": rows, "parallelism": f"replicas{world}",
+                       "l2": "no flush: per-iteration working set > 1.4 GB vs 129 MB L2"},
+            "clocks": clocks, "gpu_launches": int(mixed["kernels"]),
+            "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
+            "init_s": mixed["init_s"], "rmse": {"sample": mixed["rmse"][0], "mean": mixed["rmse"][1]},
+            "bins": {"users": mixed["info"][0][0].tolist(), "movies": mixed["info"][1][0].tolist(),
+                     "fp64_rows": [mixed["info"][0][1], mixed["info"][1][1]]},
+            "plain_fp32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reference_arm(args, world, rank):
+    """The FP64 CPU oracle as the reference arm, on bounded samples."""
+    if rank != 0:
+        return
+    ds = load_workload(args.workload, args.seed, "cuda" if _cuda() else "cpu")
+    K = ds.K
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_rate(ds, K, min(args.cpu_budget, 5.0), seed=99)
+    rates = []
+    t0 = time.perf_counter()
+    sample = cores = None
+    for k in range(args.steps):
+        r, sample, cores, _ = cpu_oracle_rate(ds, K, args.cpu_budget, seed=k)
+        rates.append(r)
+    elapsed = time.perf_counter() - t0
+    value = statistics.mean(rates)
+    ms = (ds.M + ds.N) / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Netflix-shaped ratings)",
+            "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train ratings, K={K}",
+                       "global_batch": ds.M + ds.N, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": elapsed}
+    print(json.dumps(line))
+
+
+def _cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+if __name__ == "__main__":
+    main()

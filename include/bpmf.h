@@ -1,0 +1,210 @@
+/*
+ * bpmf.h -- C ABI of the GB300 BPMF Gibbs sampler.
+ *
+ * The problem (paper Sec. I): a sparse rating matrix R of M users x N movies is
+ * approximated by U V^T with U (M x K) and V (N x K), K << M, N.  BPMF (paper
+ * Sec. II) gives every row of U and of V a Gaussian prior whose mean and
+ * precision carry a Normal-Wishart hyperprior, and samples all of them with a
+ * Gibbs sampler (Algorithm 1): per iteration, the hyperparameters of one side
+ * from that side's factors, every row of that side from its ratings and the
+ * other side's factors plus Gaussian noise, the same for the other side, then
+ * a prediction of every test point.
+ *
+ * Conventions used by every entry point
+ *  - Side 0 (BPMF_USERS) is U, the rows of R; side 1 (BPMF_MOVIES) is V, the
+ *    columns of R.
+ *  - Factor matrices are row-major float32 with leading dimension K
+ *    (row i is K consecutive floats).  Hyperparameters are float64.
+ *  - Array arguments are host pointers unless the call's `flags` holds
+ *    BPMF_DEVPTR; then they are device pointers on the handle's device.
+ *    Arrays are borrowed only for the duration of the call; the handle owns
+ *    every buffer it allocates and bpmf_destroy frees them.
+ *  - All work is queued on the CUDA stream given to bpmf_init (NULL = the
+ *    legacy default stream).  Calls that return data or a status synchronise
+ *    that stream before returning.
+ *  - Every call returns BPMF_OK (0) or a negative status; bpmf_strerror names
+ *    it and bpmf_last_error gives a one-line detail.  No call throws, aborts
+ *    or exits.  A handle is used by one host thread at a time.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *    seed, with counter (index, iteration, sub-index, stream << 8 | side), so
+ *    a draw depends only on (seed, iteration, side, row, k): results do not
+ *    depend on launch shapes or scheduling.
+ */
+#ifndef BPMF_H
+#define BPMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BPMF_API __attribute__((visibility("default")))
+#else
+#define BPMF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define BPMF_OK 0
+#define BPMF_EINVAL (-1)  /* bad argument: shape, index out of range, K, prior */
+#define BPMF_ENOMEM (-2)  /* device or host allocation failed */
+#define BPMF_ECUDA (-3)   /* a CUDA runtime call failed */
+#define BPMF_ENOTPD (-4)  /* a precision matrix was not positive definite even in FP64 */
+#define BPMF_ERNG (-5)    /* the Gamma sampler exceeded its rejection cap (64) */
+#define BPMF_ESTATE (-6)  /* call out of order (e.g. a sweep before any hyper draw) */
+
+/* ---- sides ---- */
+#define BPMF_USERS 0
+#define BPMF_MOVIES 1
+
+/* ---- execution paths (bpmf_config.path) ---- */
+#define BPMF_PATH_PLAIN 0  /* one CTA per row, FP32 FMA Gram, no degree bins */
+#define BPMF_PATH_BINNED 1 /* degree-binned launch, FP32 FMA Gram */
+#define BPMF_PATH_MIXED 2  /* degree-binned, BF16 hi/lo tensor-core Gram on heavy rows */
+
+/* ---- flags ---- */
+#define BPMF_DEVPTR 1u     /* array arguments of this call are device pointers */
+
+typedef struct bpmf bpmf_t;
+
+/* Model and sampler settings.  The Normal-Wishart hyperprior (paper Sec. II)
+ * is (mu0, beta0, W0, nu0): Lambda ~ Wishart(W0, nu0), mu | Lambda ~
+ * N(mu0, (beta0 Lambda)^-1).  mu0 (K doubles) and W0 (K x K doubles,
+ * row-major, symmetric positive definite) are host pointers read during
+ * bpmf_init only; NULL selects mu0 = 0 and W0 = I. */
+typedef struct {
+  int32_t K;          /* latent dimension, 1..128 */
+  int32_t path;       /* BPMF_PATH_* */
+  double alpha;       /* observation precision (1 / noise variance), > 0 */
+  double beta0;       /* > 0 */
+  double nu0;         /* > K - 1 */
+  const double *mu0;  /* K, or NULL */
+  const double *W0;   /* K*K, or NULL */
+  uint64_t seed;      /* Philox key */
+  int32_t order;      /* 0: users then movies in an iteration; 1: movies then users */
+  int32_t burnin;     /* iterations before the running mean of predictions starts */
+  int32_t light_max;  /* rows with degree <= light_max take the light kernel; -1: automatic */
+  int32_t hub_min;    /* rows with degree >= hub_min are split across CTAs; -1: automatic */
+} bpmf_config;
+
+/* Fills `cfg` with the defaults: path MIXED, alpha 2, beta0 2, nu0 K,
+ * mu0 = 0, W0 = I, seed 0, order 0, burnin 0, automatic thresholds. */
+BPMF_API void bpmf_config_default(bpmf_config *cfg, int32_t K);
+
+/* Creates a sampler for the M x N training ratings given as nnz triples
+ * (row[e], col[e], val[e]) (paper Sec. I; Algorithm 1's R).  Triples must be
+ * distinct cells with 0 <= row < M, 0 <= col < N; 0 <= nnz < 2^31.
+ * The call centres the ratings by their mean, builds the row-compressed
+ * (users) and column-compressed (movies) structure on the device with a
+ * stable sort (a row's ratings keep their input order), orders each side's
+ * rows by degree, and initialises U and V to 0.1 z (Philox stream 4).
+ * `stream` is a cudaStream_t (NULL: legacy default stream).
+ * Errors: EINVAL (shape, index, K, prior not SPD), ENOMEM, ECUDA. */
+BPMF_API int bpmf_init(bpmf_t **out, int64_t M, int64_t N, int64_t nnz, const int32_t *row,
+              const int32_t *col, const float *val, const bpmf_config *cfg, void *stream,
+              uint32_t flags);
+
+/* Registers n held-out test triples (Algorithm 1, "for all test points").
+ * After it, each bpmf_step predicts them and keeps the running mean of the
+ * predictions from iteration `burnin` on.  Replaces any earlier test set.
+ * Errors: EINVAL (index out of range), ENOMEM, ECUDA. */
+BPMF_API int bpmf_set_test(bpmf_t *h, int64_t n, const int32_t *row, const int32_t *col,
+                  const float *val, uint32_t flags);
+
+/* Draws the hyperparameters (mu_s, Lambda_s) of `side` from its current
+ * factor rows (Algorithm 1, "sample hyper-parameters ... based on U / V"):
+ * the Normal-Wishart posterior of the rows, Lambda_s by Bartlett's
+ * decomposition and mu_s ~ N(mu*, (beta* Lambda_s)^-1).  Reductions run in
+ * FP32 with FP64 combination; the posterior and the draw run in FP64.
+ * Errors: EINVAL (side), ENOTPD, ERNG, ECUDA. */
+BPMF_API int bpmf_sample_hyper(bpmf_t *h, int side);
+
+/* Redraws every row of `side` given the other side's current factors and
+ * the side's hyperparameters (Algorithm 1's row loops): for row i with rated
+ * neighbours j and centred ratings r_ij,
+ *   Lambda* = Lambda_s + alpha sum_j v_j v_j^T,  b = Lambda_s mu_s + alpha sum_j r_ij v_j,
+ *   L = chol(Lambda*),  u_i = L^-T (L^-1 b + z),
+ * z the K Philox normals of (seed, iteration, side, i).  Rows whose FP32
+ * pivot fails are redone in FP64.  Errors: EINVAL, ESTATE (no hyper draw for
+ * this side yet), ENOTPD, ECUDA. */
+BPMF_API int bpmf_sweep(bpmf_t *h, int side);
+
+/* One Gibbs iteration (Algorithm 1's loop body): for each side in `order`,
+ * bpmf_sample_hyper then bpmf_sweep; then the test predictions (if a test
+ * set is registered); then the iteration counter advances.  Errors: as the
+ * calls it makes. */
+BPMF_API int bpmf_step(bpmf_t *h);
+
+/* Predictions r = u_row . v_col + mean for n pairs from the current sample
+ * into out[n] (float32).  Errors: EINVAL, ECUDA. */
+BPMF_API int bpmf_predict(bpmf_t *h, int64_t n, const int32_t *row, const int32_t *col, float *out,
+                 uint32_t flags);
+
+/* Test RMSE of the latest sample and of the running mean of predictions
+ * (either pointer may be NULL).  Errors: ESTATE (no test set or no step). */
+BPMF_API int bpmf_test_rmse(bpmf_t *h, double *rmse_sample, double *rmse_mean);
+
+/* Copies the state out.  U: M*K floats, V: N*K floats, hyper: 2*(K*K + K)
+ * doubles laid out as [Lambda_U (K*K), mu_U (K), Lambda_V (K*K), mu_V (K)],
+ * iter: the iteration counter.  Any pointer may be NULL.  BPMF_DEVPTR
+ * applies to U and V only.  Errors: ECUDA. */
+BPMF_API int bpmf_get_state(bpmf_t *h, float *U, float *V, double *hyper, int64_t *iter,
+                   uint32_t flags);
+
+/* Replaces the state (same layouts as bpmf_get_state; NULL keeps a part).
+ * Setting `hyper` marks both sides' hyperparameters as drawn.
+ * Errors: EINVAL (Lambda not SPD), ECUDA. */
+BPMF_API int bpmf_set_state(bpmf_t *h, const float *U, const float *V, const double *hyper,
+                   int64_t iter, uint32_t flags);
+
+/* Copies one side's compressed structure (for checking): ptr (R+1 int64),
+ * idx (nnz int32), val (nnz float32, centred), perm (R int32, rows by degree,
+ * largest first, ties by row id), and the mean.  NULL skips a part.
+ * Errors: EINVAL, ECUDA. */
+BPMF_API int bpmf_get_structure(bpmf_t *h, int side, int64_t *ptr, int32_t *idx, float *val,
+                       int32_t *perm, double *mean);
+
+/* Last hyperparameter statistics of `side`: the row mean xbar (K) and the
+ * centred scatter S = sum (x - xbar)(x - xbar)^T (K*K), as float64.
+ * Errors: EINVAL, ESTATE, ECUDA. */
+BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
+
+/* Work counters of the last sweep of `side`: rows per bin
+ * [tiny, light, heavy, hub] and the number of rows redone in FP64. */
+BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *fp64_rows);
+
+/* ---- kernel timers (bpmf_get_timing) ---- */
+#define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */
+#define BPMF_T_HYPER_DRAW 1    /* FP64 Normal-Wishart draw */
+#define BPMF_T_ROWS_USERS 2    /* row-update kernels of the users side */
+#define BPMF_T_ROWS_MOVIES 3   /* row-update kernels of the movies side */
+#define BPMF_T_FP64_REDO 4     /* FP64 redo of flagged rows */
+#define BPMF_T_PREDICT 5       /* test predictions and RMSE */
+#define BPMF_NUM_TIMERS 6
+
+/* Turns per-phase CUDA-event timing on (1) or off (0) and clears the
+ * accumulated times.  When on, each timed phase is bracketed by two events
+ * recorded on the handle's stream.  Errors: EINVAL, ECUDA. */
+BPMF_API int bpmf_set_timing(bpmf_t *h, int enable);
+
+/* Accumulated milliseconds and launch counts per timer since timing was
+ * enabled (arrays of BPMF_NUM_TIMERS), and the total number of kernels the
+ * library launched since then (NULL skips any output).  Synchronises the
+ * stream.  Errors: EINVAL, ESTATE (timing off), ECUDA. */
+BPMF_API int bpmf_get_timing(bpmf_t *h, double *ms, int64_t *phase_count, int64_t *kernels);
+
+/* Frees the handle and all its device memory.  NULL is ignored. */
+BPMF_API void bpmf_destroy(bpmf_t *h);
+
+/* Static name of a status code. */
+BPMF_API const char *bpmf_strerror(int code);
+
+/* Detail of the last failure on this host thread ("" if none). */
+BPMF_API const char *bpmf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BPMF_H */

@@ -1,0 +1,378 @@
+"""GB300 BPMF Gibbs sampler: Python binding of the C ABI in include/bpmf.h.
+
+The functions here carry the same names as the C entry points and only
+marshal arguments (numpy arrays for host buffers, CUDA torch tensors for
+device buffers, which select BPMF_DEVPTR).  Every step of the sampler runs in
+the CUDA library ``_build/libbpmf_gb300.so``; there is no other backend, and
+loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "BpmfError", "Config", "lib", "build", "bpmf_config_default", "bpmf_init", "bpmf_set_test",
+    "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict", "bpmf_test_rmse",
+    "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
+    "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
+    "Sampler", "TIMERS",
+    "USERS", "MOVIES", "PATH_PLAIN", "PATH_BINNED", "PATH_MIXED", "DEVPTR",
+]
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTPD, ERNG, ESTATE = 0, -1, -2, -3, -4, -5, -6
+USERS, MOVIES = 0, 1
+PATH_PLAIN, PATH_BINNED, PATH_MIXED = 0, 1, 2
+DEVPTR = 1
+
+SYMBOLS = [
+    "bpmf_config_default", "bpmf_init", "bpmf_set_test", "bpmf_sample_hyper", "bpmf_sweep",
+    "bpmf_step", "bpmf_predict", "bpmf_test_rmse", "bpmf_get_state", "bpmf_set_state",
+    "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
+    "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
+]
+TIMERS = ["hyper_reduce", "hyper_draw", "rows_users", "rows_movies", "fp64_redo", "predict"]
+
+
+class BpmfError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = f"{where}: {bpmf_strerror(code)} ({code})"
+        detail = lib().bpmf_last_error().decode() if _lib is not None else ""
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("K", C.c_int32), ("path", C.c_int32), ("alpha", C.c_double), ("beta0", C.c_double),
+        ("nu0", C.c_double), ("mu0", C.c_void_p), ("W0", C.c_void_p), ("seed", C.c_uint64),
+        ("order", C.c_int32), ("burnin", C.c_int32), ("light_max", C.c_int32),
+        ("hub_min", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (nvcc) if it is missing or stale."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded CUDA library.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library {path} is not built; call paper_1705_04159_gb300.build()")
+        L = C.CDLL(path)
+        P, i64, i32, u32 = C.c_void_p, C.c_int64, C.c_int32, C.c_uint32
+        L.bpmf_config_default.argtypes = [C.POINTER(Config), i32]
+        L.bpmf_config_default.restype = None
+        L.bpmf_init.argtypes = [C.POINTER(C.c_void_p), i64, i64, i64, P, P, P, C.POINTER(Config),
+                                P, u32]
+        L.bpmf_set_test.argtypes = [P, i64, P, P, P, u32]
+        L.bpmf_sample_hyper.argtypes = [P, C.c_int]
+        L.bpmf_sweep.argtypes = [P, C.c_int]
+        L.bpmf_step.argtypes = [P]
+        L.bpmf_predict.argtypes = [P, i64, P, P, P, u32]
+        L.bpmf_test_rmse.argtypes = [P, P, P]
+        L.bpmf_get_state.argtypes = [P, P, P, P, P, u32]
+        L.bpmf_set_state.argtypes = [P, P, P, P, i64, u32]
+        L.bpmf_get_structure.argtypes = [P, C.c_int, P, P, P, P, P]
+        L.bpmf_get_hyper_stats.argtypes = [P, C.c_int, P, P]
+        L.bpmf_get_sweep_info.argtypes = [P, C.c_int, P, P]
+        L.bpmf_set_timing.argtypes = [P, C.c_int]
+        L.bpmf_get_timing.argtypes = [P, P, P, P]
+        L.bpmf_destroy.argtypes = [P]
+        L.bpmf_destroy.restype = None
+        L.bpmf_strerror.argtypes = [C.c_int]
+        L.bpmf_strerror.restype = C.c_char_p
+        L.bpmf_last_error.argtypes = []
+        L.bpmf_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------ marshalling --
+
+def _is_cuda_tensor(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive, is_device) for a numpy array or a CUDA tensor."""
+    if x is None:
+        return None, None, False
+    if _is_cuda_tensor(x):
+        import torch
+        want = {np.int32: torch.int32, np.float32: torch.float32, np.int64: torch.int64,
+                np.float64: torch.float64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"device tensor must be contiguous {want}")
+        return x.data_ptr(), x, True
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a, False
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise BpmfError(rc, where)
+
+
+# ------------------------------------------------------- C-named wrappers --
+
+def bpmf_strerror(code: int) -> str:
+    return lib().bpmf_strerror(code).decode()
+
+
+def bpmf_config_default(K: int) -> Config:
+    cfg = Config()
+    lib().bpmf_config_default(C.byref(cfg), K)
+    return cfg
+
+
+def bpmf_init(M, N, row, col, val, cfg: Config, stream=None, mu0=None, W0=None):
+    """Returns an opaque handle (int).  Device tensors select BPMF_DEVPTR."""
+    pr, kr, dr = _ptr(row, np.int32)
+    pc, kc, dc = _ptr(col, np.int32)
+    pv, kv, dv = _ptr(val, np.float32)
+    if len({dr, dc, dv}) != 1:
+        raise TypeError("row, col and val must all be host arrays or all device tensors")
+    nnz = int(len(row))
+    keep = []
+    if mu0 is not None:
+        m = np.ascontiguousarray(mu0, np.float64)
+        keep.append(m)
+        cfg.mu0 = m.ctypes.data
+    if W0 is not None:
+        w = np.ascontiguousarray(W0, np.float64)
+        keep.append(w)
+        cfg.W0 = w.ctypes.data
+    h = C.c_void_p()
+    rc = lib().bpmf_init(C.byref(h), int(M), int(N), nnz, pr, pc, pv, C.byref(cfg),
+                         _stream_ptr(stream), DEVPTR if dr else 0)
+    cfg.mu0 = None
+    cfg.W0 = None
+    _check(rc, "bpmf_init")
+    return h.value
+
+
+def bpmf_set_test(h, row, col, val):
+    pr, kr, dr = _ptr(row, np.int32)
+    pc, kc, dc = _ptr(col, np.int32)
+    pv, kv, dv = _ptr(val, np.float32)
+    _check(lib().bpmf_set_test(h, int(len(row)), pr, pc, pv, DEVPTR if dr else 0), "bpmf_set_test")
+
+
+def bpmf_sample_hyper(h, side):
+    _check(lib().bpmf_sample_hyper(h, side), "bpmf_sample_hyper")
+
+
+def bpmf_sweep(h, side):
+    _check(lib().bpmf_sweep(h, side), "bpmf_sweep")
+
+
+def bpmf_step(h):
+    _check(lib().bpmf_step(h), "bpmf_step")
+
+
+def bpmf_predict(h, row, col, out=None):
+    n = int(len(row))
+    pr, kr, dr = _ptr(row, np.int32)
+    pc, kc, dc = _ptr(col, np.int32)
+    if out is None:
+        if dr:
+            import torch
+            out = torch.empty(n, dtype=torch.float32, device=row.device)
+        else:
+            out = np.empty(n, np.float32)
+    po, ko, do = _ptr(out, np.float32)
+    _check(lib().bpmf_predict(h, n, pr, pc, po, DEVPTR if dr else 0), "bpmf_predict")
+    return out
+
+
+def bpmf_test_rmse(h):
+    a = C.c_double()
+    b = C.c_double()
+    _check(lib().bpmf_test_rmse(h, C.byref(a), C.byref(b)), "bpmf_test_rmse")
+    return a.value, b.value
+
+
+def bpmf_get_state(h, M, N, K, U=None, V=None):
+    """Returns (U, V, hyper, iter); U/V may be given as CUDA tensors (DEVPTR)."""
+    dev = _is_cuda_tensor(U)
+    if U is None:
+        U = np.empty((M, K), np.float32)
+    if V is None:
+        V = np.empty((N, K), np.float32)
+    hyper = np.empty(2 * (K * K + K), np.float64)
+    it = C.c_int64()
+    pu, ku, _ = _ptr(U, np.float32)
+    pv, kv, _ = _ptr(V, np.float32)
+    _check(lib().bpmf_get_state(h, pu, pv, hyper.ctypes.data, C.byref(it), DEVPTR if dev else 0),
+           "bpmf_get_state")
+    return U, V, hyper, it.value
+
+
+def bpmf_set_state(h, U=None, V=None, hyper=None, it=0):
+    dev = _is_cuda_tensor(U) or _is_cuda_tensor(V)
+    pu, ku, _ = _ptr(U, np.float32)
+    pv, kv, _ = _ptr(V, np.float32)
+    hy = None if hyper is None else np.ascontiguousarray(hyper, np.float64)
+    _check(lib().bpmf_set_state(h, pu, pv, None if hy is None else hy.ctypes.data, int(it),
+                                DEVPTR if dev else 0), "bpmf_set_state")
+
+
+def bpmf_get_structure(h, side, R, nnz):
+    ptr = np.empty(R + 1, np.int64)
+    idx = np.empty(max(nnz, 1), np.int32)
+    val = np.empty(max(nnz, 1), np.float32)
+    perm = np.empty(R, np.int32)
+    mean = C.c_double()
+    _check(lib().bpmf_get_structure(h, side, ptr.ctypes.data, idx.ctypes.data, val.ctypes.data,
+                                    perm.ctypes.data, C.byref(mean)), "bpmf_get_structure")
+    return ptr, idx[:nnz], val[:nnz], perm, mean.value
+
+
+def bpmf_get_hyper_stats(h, side, K):
+    xbar = np.empty(K)
+    S = np.empty((K, K))
+    _check(lib().bpmf_get_hyper_stats(h, side, xbar.ctypes.data, S.ctypes.data),
+           "bpmf_get_hyper_stats")
+    return xbar, S
+
+
+def bpmf_get_sweep_info(h, side):
+    bins = np.zeros(4, np.int64)
+    f = C.c_int64()
+    _check(lib().bpmf_get_sweep_info(h, side, bins.ctypes.data, C.byref(f)), "bpmf_get_sweep_info")
+    return bins, f.value
+
+
+def bpmf_set_timing(h, enable=True):
+    _check(lib().bpmf_set_timing(h, 1 if enable else 0), "bpmf_set_timing")
+
+
+def bpmf_get_timing(h):
+    """({timer: ms}, {timer: phases}, kernels launched) since timing was enabled."""
+    ms = np.zeros(len(TIMERS))
+    cnt = np.zeros(len(TIMERS), np.int64)
+    k = C.c_int64()
+    _check(lib().bpmf_get_timing(h, ms.ctypes.data, cnt.ctypes.data, C.byref(k)),
+           "bpmf_get_timing")
+    return dict(zip(TIMERS, ms.tolist())), dict(zip(TIMERS, cnt.tolist())), k.value
+
+
+def bpmf_destroy(h):
+    if h:
+        lib().bpmf_destroy(h)
+
+
+# -------------------------------------------------------------- wrapper --
+
+class Sampler:
+    """A BPMF sampler on the current CUDA device (one handle of the C ABI)."""
+
+    def __init__(self, M, N, row, col, val, K, alpha=2.0, beta0=2.0, nu0=None, mu0=None, W0=None,
+                 seed=0, path=PATH_MIXED, order=0, burnin=0, light_max=-1, hub_min=-1,
+                 stream=None):
+        cfg = bpmf_config_default(K)
+        cfg.alpha = float(alpha)
+        cfg.beta0 = float(beta0)
+        cfg.nu0 = float(K if nu0 is None else nu0)
+        cfg.seed = int(seed)
+        cfg.path = int(path)
+        cfg.order = int(order)
+        cfg.burnin = int(burnin)
+        cfg.light_max = int(light_max)
+        cfg.hub_min = int(hub_min)
+        self.M, self.N, self.K = int(M), int(N), int(K)
+        self.nnz = int(len(row))
+        self.h = bpmf_init(M, N, row, col, val, cfg, stream=stream, mu0=mu0, W0=W0)
+
+    def close(self):
+        if self.h:
+            bpmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_test(self, row, col, val):
+        bpmf_set_test(self.h, row, col, val)
+
+    def sample_hyper(self, side):
+        bpmf_sample_hyper(self.h, side)
+
+    def sweep(self, side):
+        bpmf_sweep(self.h, side)
+
+    def step(self):
+        bpmf_step(self.h)
+
+    def predict(self, row, col, out=None):
+        return bpmf_predict(self.h, row, col, out)
+
+    def test_rmse(self):
+        return bpmf_test_rmse(self.h)
+
+    def get_state(self, U=None, V=None):
+        return bpmf_get_state(self.h, self.M, self.N, self.K, U, V)
+
+    def set_state(self, U=None, V=None, hyper=None, it=0):
+        bpmf_set_state(self.h, U, V, hyper, it)
+
+    def structure(self, side):
+        R = self.M if side == USERS else self.N
+        return bpmf_get_structure(self.h, side, R, self.nnz)
+
+    def hyper_stats(self, side):
+        return bpmf_get_hyper_stats(self.h, side, self.K)
+
+    def sweep_info(self, side):
+        return bpmf_get_sweep_info(self.h, side)
+
+    def set_timing(self, enable=True):
+        bpmf_set_timing(self.h, enable)
+
+    def timing(self):
+        return bpmf_get_timing(self.h)
+
+    def hyper(self):
+        """(Lambda_U, mu_U, Lambda_V, mu_V) from the packed state."""
+        K = self.K
+        _, _, hy, _ = self.get_state(U=np.empty((self.M, K), np.float32),
+                                     V=np.empty((self.N, K), np.float32))
+        o = K * K + K
+        return (hy[:K * K].reshape(K, K), hy[K * K:o], hy[o:o + K * K].reshape(K, K),
+                hy[o + K * K:])

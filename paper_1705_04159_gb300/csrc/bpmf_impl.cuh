@@ -1,0 +1,223 @@
+// bpmf_impl.cuh -- internal declarations of the CUDA BPMF library.
+//
+// Device layout (all owned by the handle):
+//   per side s: ptr int64[R+1], idx int32[nnz], val float32[nnz] (centred
+//   ratings, compressed by row of that side), perm int32[R] (rows by degree,
+//   largest first), X float32[R * K] factors (row-major, ld K), bf16 hi/lo
+//   shadow of X for the tensor-core Gram, hyper (Lambda f64 K*K, mu f64 K,
+//   Lambda f32 K*K, b0 = Lambda mu f32 K), hyper statistics f64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "bpmf.h"
+
+namespace gb {
+
+constexpr int kMaxK = 128;
+constexpr int kGammaCap = 64;
+
+// Philox stream ids (high word of the counter's last element)
+constexpr uint32_t kStreamRow = 0u;
+constexpr uint32_t kStreamHyperMu = 1u;
+constexpr uint32_t kStreamWishart = 2u;
+constexpr uint32_t kStreamGamma = 3u;
+constexpr uint32_t kStreamInit = 4u;
+
+// device status bits
+constexpr int kStatusNotPD = 1;
+constexpr int kStatusRng = 2;
+constexpr int kStatusIndex = 4;
+
+// degree bins
+enum Bin { kBinTiny = 0, kBinLight = 1, kBinHeavy = 2, kBinHub = 3, kNumBins = 4 };
+
+struct SideDev {
+  int64_t R = 0;          // rows of this side
+  int64_t* ptr = nullptr;
+  int32_t* idx = nullptr;
+  float* val = nullptr;
+  int32_t* perm = nullptr;
+  float* X = nullptr;      // R*K
+  uint32_t* Xhl = nullptr; // R*K packed (bf16 hi | bf16 lo << 16), mixed path only
+  double* lam = nullptr;   // K*K
+  double* mu = nullptr;    // K
+  float* lamf = nullptr;   // K*K
+  float* b0f = nullptr;    // K
+  double* xbar = nullptr;  // K      (last statistics)
+  double* S = nullptr;     // K*K
+  int64_t bin_count[kNumBins] = {0, 0, 0, 0};  // rows per bin (perm order: hub, heavy, light, tiny)
+  int64_t light_max = 0, hub_min = 0;          // thresholds in effect
+  int64_t max_deg = 0;
+  bool have_hyper = false;
+  bool have_stats = false;
+  int64_t fp64_rows = 0;
+};
+
+struct Handle {
+  int64_t M = 0, N = 0, nnz = 0;
+  int K = 0;
+  bpmf_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  double mean = 0.0;
+  SideDev side[2];
+  double* mu0 = nullptr;    // K
+  double* W0inv = nullptr;  // K*K
+  // scratch
+  double* red = nullptr;    // reduction partials
+  int64_t red_len = 0;
+  double* wscr = nullptr;   // FP64 Wishart scratch (6 K*K + 8 K)
+  int* status = nullptr;    // device status word
+  int32_t* flag_rows = nullptr;  // rows flagged for the FP64 redo (max R over sides)
+  int32_t* flag_count = nullptr;
+  // test set (sorted by user for gather locality)
+  int64_t n_test = 0;
+  int32_t* trow = nullptr;
+  int32_t* tcol = nullptr;
+  float* tval = nullptr;
+  double* tsum = nullptr;    // running sum of predictions
+  double* terr = nullptr;    // [2] sample / mean squared error
+  int64_t n_avg = 0;
+  bool have_rmse = false;
+  int64_t iter = 0;
+  // hub split partial Grams
+  float* hub_part = nullptr;
+  int64_t hub_part_len = 0;
+  // phase timers (CUDA events on the handle's stream) and launch counter
+  bool timing = false;
+  struct Pending { cudaEvent_t a, b; int id; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double t_ms[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
+  int64_t t_cnt[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
+  int64_t kernels = 0;
+};
+
+// Brackets one phase with two events when timing is on (api.cu).
+struct PhaseTimer {
+  Handle* h;
+  int id;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(Handle* h_, int id_);
+  ~PhaseTimer();
+};
+int resolve_timers(Handle* h);
+void release_timers(Handle* h);
+
+// ---------------------------------------------------------------- Philox --
+// Philox4x32-10: ten rounds, each two 32x32 -> 64-bit products by the
+// round multipliers, words permuted and mixed with the key, key bumped by
+// the Weyl increments between rounds (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hiA = __umulhi(0xD2511F53u, c.x), loA = 0xD2511F53u * c.x;
+    const uint32_t hiB = __umulhi(0xCD9E8D57u, c.z), loB = 0xCD9E8D57u * c.z;
+    c = make_uint4(hiB ^ c.y ^ k.x, loB, hiA ^ c.w ^ k.y, loA);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+  return make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32));
+}
+
+// uniform in (0,1): (2 (x >> 9) + 1) 2^-24, exact in binary32
+__device__ __forceinline__ float unit_f32(uint32_t x) {
+  return __uint2float_rn(((x >> 9) << 1) | 1u) * 5.9604644775390625e-08f;
+}
+__device__ __forceinline__ double unit_f64(uint32_t x) {
+  return (double)(((x >> 9) << 1) | 1u) * 5.9604644775390625e-08;
+}
+
+// four FP32 normals from one counter: Box-Muller on (x, y) and on (z, w)
+__device__ __forceinline__ float4 normal4_f32(uint4 w) {
+  float4 o;
+  float s, c;
+  float rad = sqrtf(-2.0f * logf(unit_f32(w.x)));
+  sincospif(2.0f * unit_f32(w.y), &s, &c);
+  o.x = rad * c;
+  o.y = rad * s;
+  rad = sqrtf(-2.0f * logf(unit_f32(w.z)));
+  sincospif(2.0f * unit_f32(w.w), &s, &c);
+  o.z = rad * c;
+  o.w = rad * s;
+  return o;
+}
+
+__device__ __forceinline__ void normal2_f64(uint32_t a, uint32_t b, double& z0, double& z1) {
+  double s, c;
+  const double rad = sqrt(-2.0 * log(unit_f64(a)));
+  sincospi(2.0 * unit_f64(b), &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// normal number n of the counter base (c0, c1, ., c3) in FP64
+__device__ __forceinline__ double normal_at_f64(uint2 key, uint32_t c0, uint32_t c1, uint32_t c3,
+                                                uint32_t n) {
+  const uint4 w = philox(make_uint4(c0, c1, n >> 2, c3), key);
+  double z0, z1;
+  if ((n & 3u) < 2u) normal2_f64(w.x, w.y, z0, z1);
+  else normal2_f64(w.z, w.w, z0, z1);
+  return (n & 1u) ? z1 : z0;
+}
+
+__host__ __device__ __forceinline__ uint32_t stream_word(uint32_t stream, int side) {
+  return (stream << 8) | (uint32_t)side;
+}
+
+// ------------------------------------------------------------ launchers --
+// structure.cu
+int build_structure(Handle* h, const int32_t* d_row, const int32_t* d_col, const float* d_val);
+int sort_pairs_u32(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_out,
+                   int32_t* vals_out, int64_t n, uint32_t max_key, cudaStream_t st);
+int order_rows_by_degree(Handle* h, int s);
+double device_mean(const float* d_val, int64_t n, double* d_red, cudaStream_t st, int* err);
+int sort_test_set(Handle* h, const int32_t* d_row, const int32_t* d_col, const float* d_val,
+                  int64_t n, uint32_t* keys, uint32_t* keys_sorted, int32_t* ids, int32_t* src);
+int validate_pairs(Handle* h, const int32_t* d_row, const int32_t* d_col, int64_t n);
+int setup_bins(Handle* h, int s);
+
+// hyper.cu
+int launch_hyper(Handle* h, int s);
+int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch, int* status,
+                           cudaStream_t st);
+int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, cudaStream_t st);
+int launch_hyper_to_f32(Handle* h, int s);
+
+// rows.cu
+int launch_sweep(Handle* h, int s);
+int launch_init_factors(Handle* h, int s);
+int launch_refresh_shadow(Handle* h, int s);
+
+// predict.cu
+int launch_predict(Handle* h, int64_t n, const int32_t* r, const int32_t* c, float* out);
+int launch_test_step(Handle* h, bool accumulate);
+
+// api.cu
+void set_error(const char* fmt, ...);
+
+}  // namespace gb
+
+#define BPMF_CUDA_CHECK(call)                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      gb::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return BPMF_ECUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+
+#define BPMF_TRY(expr)      \
+  do {                      \
+    int rc_ = (expr);       \
+    if (rc_ != BPMF_OK) return rc_; \
+  } while (0)

@@ -1,0 +1,455 @@
+// hyper.cu -- hyperparameter draw of one side (Algorithm 1, "sample
+// hyper-parameters movies based on V" / "users based on U").
+//
+// BPMF's hyperprior (paper Sec. II) is Normal-Wishart: Lambda ~ W(W0, nu0),
+// mu | Lambda ~ N(mu0, (beta0 Lambda)^-1).  Given the n factor rows x_i of a
+// side, with mean xbar and centred scatter S = sum (x_i - xbar)(x_i - xbar)^T,
+// the posterior is Normal-Wishart with
+//   beta* = beta0 + n, nu* = nu0 + n, mu* = (beta0 mu0 + n xbar) / (beta0 + n),
+//   W*^-1 = W0^-1 + S + beta0 n / (beta0 + n) (mu0 - xbar)(mu0 - xbar)^T.
+// Lambda is drawn by Bartlett's decomposition (C = chol(W*), A lower with
+// A_kk^2 ~ chi^2(nu* - k), A_kl ~ N(0,1); Lambda = (C A)(C A)^T) and
+// mu = mu* + chol(beta* Lambda)^-T z.
+//
+// Device work: (1) column sums of the factor rows with FP32 partials per block
+// combined in FP64; (2) the centred scatter, a K x K Gram over all rows with
+// FP32 register tiles per block, combined in FP64 in a fixed block order;
+// (3) one CTA in FP64 for the posterior, the three Cholesky factorisations, the
+// triangular inverse and the draws (O(K^3), independent of the row count).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bpmf_impl.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// ---- (1) column sums: part[b * K + k] = sum over block b's rows of x[., k]
+__global__ void colsum_partial(const float* __restrict__ X, int64_t R, int K,
+                               double* __restrict__ part) {
+  __shared__ double half[kMaxK];
+  const int k = threadIdx.x & (kMaxK - 1);
+  const int grp = threadIdx.x >> 7;  // 2 row groups of 128 threads
+  const int64_t per = (R + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(R, r0 + per);
+  double acc = 0.0;
+  if (k < K) {
+    float chunk = 0.f;
+    int cnt = 0;
+    for (int64_t r = r0 + grp; r < r1; r += 2) {
+      chunk += X[r * K + k];
+      if (++cnt == 64) {
+        acc += (double)chunk;
+        chunk = 0.f;
+        cnt = 0;
+      }
+    }
+    acc += (double)chunk;
+  }
+  if (grp == 1) half[k] = acc;
+  __syncthreads();
+  if (grp == 0 && k < K) part[(int64_t)blockIdx.x * K + k] = acc + half[k];
+}
+
+__global__ void colsum_final(const double* __restrict__ part, int blocks, int K, int64_t R,
+                             double* __restrict__ xbar, float* __restrict__ xbarf) {
+  const int k = threadIdx.x;
+  if (k < K) {
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * K + k];
+    s /= (double)R;
+    xbar[k] = s;
+    xbarf[k] = (float)s;
+  }
+}
+
+// ---- (2) centred scatter.  Thread (ty, tx) of a 16 x 16 grid owns the TM x TM
+// tile at rows ty*TM.., cols tx*TM..; only tiles with ty >= tx (the lower
+// triangle) are accumulated; the upper triangle is mirrored at the end.
+template <int TM>
+__global__ void __launch_bounds__(256) scatter_partial(const float* __restrict__ X, int64_t R,
+                                                       int K, const float* __restrict__ xbarf,
+                                                       double* __restrict__ part) {
+  constexpr int KP = 16 * TM;
+  constexpr int CH = 32;
+  __shared__ float xs[CH][KP + 1];
+  const int tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
+  const bool active = ty >= tx;
+  const int64_t per = (R + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = min(R, r0 + per);
+  float acc[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TM; ++b) acc[a][b] = 0.f;
+  for (int64_t c0 = r0; c0 < r1; c0 += CH) {
+    const int cnt = (int)min((int64_t)CH, r1 - c0);
+    __syncthreads();
+    for (int e = tid; e < CH * KP; e += 256) {
+      const int rr = e / KP, k = e % KP;
+      float v = 0.f;
+      if (rr < cnt && k < K) v = X[(c0 + rr) * K + k] - xbarf[k];
+      xs[rr][k] = v;
+    }
+    __syncthreads();
+    if (active) {
+      for (int rr = 0; rr < cnt; ++rr) {
+        float a[TM], b[TM];
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+          a[q] = xs[rr][ty * TM + q];
+          b[q] = xs[rr][tx * TM + q];
+        }
+#pragma unroll
+        for (int p = 0; p < TM; ++p)
+#pragma unroll
+          for (int q = 0; q < TM; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+      }
+    }
+  }
+  if (active) {
+    double* out = part + (int64_t)blockIdx.x * K * K;
+#pragma unroll
+    for (int p = 0; p < TM; ++p)
+#pragma unroll
+      for (int q = 0; q < TM; ++q) {
+        const int i = ty * TM + p, j = tx * TM + q;
+        if (i < K && j < K && j <= i) out[i * K + j] = (double)acc[p][q];
+      }
+  }
+}
+
+__global__ void scatter_final(const double* __restrict__ part, int blocks, int K,
+                              double* __restrict__ S) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K * K) return;
+  const int i = e / K, j = e % K;
+  if (j > i) return;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * K * K + i * K + j];
+  S[i * K + j] = s;
+  S[j * K + i] = s;
+}
+
+// ---- (3) FP64 dense algebra by one CTA on row-major K x K matrices in
+// global scratch.  Every helper starts and ends with the block synchronised.
+
+// In-place lower Cholesky (upper part zeroed).  Returns false (to all
+// threads) if a pivot is not positive.
+__device__ bool cta_cholesky(double* A, int K, int* bad) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int k = 0; k < K; ++k) {
+    const double piv = A[k * K + k];
+    const double d = piv > 0.0 ? sqrt(piv) : 1.0;
+    __syncthreads();
+    if (!(piv > 0.0)) {
+      if (tid == 0) *bad = 1;
+    }
+    for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] /= d;
+    if (tid == 0) A[k * K + k] = d;
+    __syncthreads();
+    const int m = K - k - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) A[i * K + j] -= A[i * K + k] * A[j * K + k];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < K * K; e += nt) {
+    const int i = e / K, j = e % K;
+    if (j > i) A[e] = 0.0;
+  }
+  __syncthreads();
+  const bool ok = *bad == 0;
+  __syncthreads();
+  return ok;
+}
+
+// Linv = L^-1 for lower-triangular L: thread j solves column j by forward
+// substitution.
+__device__ void cta_tri_inverse(const double* L, double* Linv, int K) {
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    for (int i = 0; i < K; ++i) {
+      double v;
+      if (i < j) v = 0.0;
+      else {
+        double t = (i == j) ? 1.0 : 0.0;
+        for (int k = j; k < i; ++k) t -= L[i * K + k] * Linv[k * K + j];
+        v = t / L[i * K + i];
+      }
+      Linv[i * K + j] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// C = A^T A (symmetric)
+__device__ void cta_ata(const double* A, double* C, int K) {
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += A[k * K + i] * A[k * K + j];
+    C[e] = s;
+  }
+  __syncthreads();
+}
+
+// Bartlett factor of Wishart(W, nu) with W = C C^T (C lower, given):
+// B = C A, then Lambda = B B^T.  Gamma draws by Marsaglia-Tsang with the
+// attempt number as the counter's third word; the cap flags kStatusRng.
+__device__ void cta_bartlett(const double* C, double* A, double* B, double* Lam, int K, double nu,
+                             uint2 key, uint32_t t, int side, int* status) {
+  const uint32_t sw_w = stream_word(kStreamWishart, side);
+  const uint32_t sw_g = stream_word(kStreamGamma, side);
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int k = e / K, l = e % K;
+    double v = 0.0;
+    if (l < k) v = normal_at_f64(key, 0u, t, sw_w, (uint32_t)(k * (k - 1) / 2 + l));
+    A[e] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double shape = 0.5 * (nu - (double)k);
+    const double s = shape < 1.0 ? shape + 1.0 : shape;
+    const double d = s - 1.0 / 3.0;
+    const double c = 1.0 / sqrt(9.0 * d);
+    double g = -1.0;
+    for (int a = 0; a < kGammaCap && g < 0.0; ++a) {
+      const uint4 w = philox(make_uint4((uint32_t)k, t, (uint32_t)a, sw_g), key);
+      double zn, zs;
+      normal2_f64(w.x, w.y, zn, zs);
+      double v = 1.0 + c * zn;
+      if (v <= 0.0) continue;
+      v = v * v * v;
+      const double u = unit_f64(w.z);
+      if (log(u) < 0.5 * zn * zn + d - d * v + d * log(v)) {
+        g = d * v;
+        if (shape < 1.0) g *= pow(unit_f64(w.w), 1.0 / shape);
+      }
+    }
+    if (g < 0.0) {
+      atomicOr(status, kStatusRng);
+      g = s;
+    }
+    A[k * K + k] = sqrt(2.0 * g);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    double v = 0.0;
+    if (j <= i)
+      for (int m = j; m <= i; ++m) v += C[i * K + m] * A[m * K + j];
+    B[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    const int top = min(i, j);
+    double v = 0.0;
+    for (int m = 0; m <= top; ++m) v += B[i * K + m] * B[j * K + m];
+    Lam[e] = v;
+  }
+  __syncthreads();
+}
+
+struct HyperArgs {
+  const double* xbar;
+  const double* S;
+  int64_t n;
+  const double* mu0;
+  double beta0, nu0;
+  const double* W0inv;
+  uint64_t seed;
+  uint32_t t;
+  int side;
+  int K;
+  double* scr;  // 6 K*K + 2 K doubles
+  double* lam;
+  double* mu;
+  float* lamf;
+  float* b0f;
+  int* status;
+};
+
+__global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
+  __shared__ int bad;
+  const int K = a.K, KK = K * K;
+  double* Wi = a.scr;          // W*^-1, then its Cholesky factor P
+  double* Pinv = Wi + KK;      // P^-1
+  double* Ws = Pinv + KK;      // W*, then C = chol(W*)
+  double* A = Ws + KK;         // Bartlett A
+  double* B = A + KK;          // C A
+  double* Lm = B + KK;         // chol(beta* Lambda)
+  double* mus = Lm + KK;       // mu*
+  double* x = mus + K;         // solve workspace
+  const double n = (double)a.n;
+  const double w = a.beta0 * n / (a.beta0 + n);
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    Wi[e] = a.W0inv[e] + a.S[e] + w * (a.mu0[i] - a.xbar[i]) * (a.mu0[j] - a.xbar[j]);
+  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    mus[k] = (a.beta0 * a.mu0[k] + n * a.xbar[k]) / (a.beta0 + n);
+  __syncthreads();
+  const double beta_s = a.beta0 + n, nu_s = a.nu0 + n;
+  if (!cta_cholesky(Wi, K, &bad)) {
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
+    return;
+  }
+  cta_tri_inverse(Wi, Pinv, K);
+  cta_ata(Pinv, Ws, K);  // W* = P^-T P^-1
+  if (!cta_cholesky(Ws, K, &bad)) {
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
+    return;
+  }
+  const uint2 key = seed_key(a.seed);
+  cta_bartlett(Ws, A, B, a.lam, K, nu_s, key, a.t, a.side, a.status);
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) Lm[e] = beta_s * a.lam[e];
+  __syncthreads();
+  if (!cta_cholesky(Lm, K, &bad)) {
+    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
+    return;
+  }
+  // mu = mu* + Lm^-T z, back substitution by one thread (K <= 128 steps)
+  if (threadIdx.x == 0) {
+    const uint32_t sw = stream_word(kStreamHyperMu, a.side);
+    for (int i = K - 1; i >= 0; --i) {
+      double v = normal_at_f64(key, 0u, a.t, sw, (uint32_t)i);
+      for (int k = i + 1; k < K; ++k) v -= Lm[k * K + i] * x[k];
+      x[i] = v / Lm[i * K + i];
+    }
+    for (int i = 0; i < K; ++i) a.mu[i] = mus[i] + x[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) a.lamf[e] = (float)a.lam[e];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += a.lam[i * K + k] * a.mu[k];
+    a.b0f[i] = (float)s;
+  }
+}
+
+// Ainv = A^-1 for SPD A (used once for W0^-1); flags kStatusNotPD.
+__global__ void __launch_bounds__(512) spd_inverse_kernel(const double* A, double* Ainv, int K,
+                                                          double* scr, int* status) {
+  __shared__ int bad;
+  const int KK = K * K;
+  double* L = scr;
+  double* Li = scr + KK;
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) L[e] = A[e];
+  __syncthreads();
+  if (!cta_cholesky(L, K, &bad)) {
+    if (threadIdx.x == 0) atomicOr(status, kStatusNotPD);
+    return;
+  }
+  cta_tri_inverse(L, Li, K);
+  cta_ata(Li, Ainv, K);
+}
+
+__global__ void __launch_bounds__(512) spd_check_kernel(const double* A, int K, double* scr,
+                                                        int* status) {
+  __shared__ int bad;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) scr[e] = A[e];
+  __syncthreads();
+  if (!cta_cholesky(scr, K, &bad) && threadIdx.x == 0) atomicOr(status, kStatusNotPD);
+}
+
+// float copies of a side's hyperparameters (after bpmf_set_state)
+__global__ void hyper_f32(const double* lam, const double* mu, int K, float* lamf, float* b0f) {
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) lamf[e] = (float)lam[e];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += lam[i * K + k] * mu[k];
+    b0f[i] = (float)s;
+  }
+}
+
+template <int TM>
+void launch_scatter(const float* X, int64_t R, int K, const float* xbarf, double* part, int blocks,
+                    cudaStream_t st) {
+  scatter_partial<TM><<<blocks, 256, 0, st>>>(X, R, K, xbarf, part);
+}
+
+}  // namespace
+
+int launch_hyper(Handle* h, int s) {
+  SideDev& sd = h->side[s];
+  const int K = h->K;
+  cudaStream_t st = h->stream;
+  const int64_t R = sd.R;
+  // blocks: up to 2 per SM, at least 64 rows each
+  int blocks = 2 * h->num_sms;
+  if ((int64_t)blocks * 64 > R) blocks = (int)std::max<int64_t>(1, (R + 63) / 64);
+  double* part = h->red;  // holds blocks * K * K doubles (sized at init)
+  float* xbarf = reinterpret_cast<float*>(h->wscr + 6 * K * K + 4 * K);
+  {
+    PhaseTimer timer(h, BPMF_T_HYPER_REDUCE);
+    colsum_partial<<<blocks, kRedThreads, 0, st>>>(sd.X, R, K, part);
+    colsum_final<<<1, kMaxK, 0, st>>>(part, blocks, K, R, sd.xbar, xbarf);
+    if (K <= 16) launch_scatter<1>(sd.X, R, K, xbarf, part, blocks, st);
+    else if (K <= 32) launch_scatter<2>(sd.X, R, K, xbarf, part, blocks, st);
+    else if (K <= 64) launch_scatter<4>(sd.X, R, K, xbarf, part, blocks, st);
+    else if (K <= 112) launch_scatter<7>(sd.X, R, K, xbarf, part, blocks, st);
+    else launch_scatter<8>(sd.X, R, K, xbarf, part, blocks, st);
+    scatter_final<<<(K * K + 255) / 256, 256, 0, st>>>(part, blocks, K, sd.S);
+    BPMF_CUDA_CHECK(cudaGetLastError());
+    h->kernels += 4;
+  }
+  HyperArgs a;
+  a.xbar = sd.xbar;
+  a.S = sd.S;
+  a.n = R;
+  a.mu0 = h->mu0;
+  a.beta0 = h->cfg.beta0;
+  a.nu0 = h->cfg.nu0;
+  a.W0inv = h->W0inv;
+  a.seed = h->cfg.seed;
+  a.t = (uint32_t)h->iter;
+  a.side = s;
+  a.K = K;
+  a.scr = h->wscr;
+  a.lam = sd.lam;
+  a.mu = sd.mu;
+  a.lamf = sd.lamf;
+  a.b0f = sd.b0f;
+  a.status = h->status;
+  {
+    PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
+    wishart_draw<<<1, 512, 0, st>>>(a);
+    BPMF_CUDA_CHECK(cudaGetLastError());
+    h->kernels += 1;
+  }
+  sd.have_hyper = true;
+  sd.have_stats = true;
+  return BPMF_OK;
+}
+
+int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch, int* status,
+                           cudaStream_t st) {
+  spd_inverse_kernel<<<1, 512, 0, st>>>(A, Ainv, K, scratch, status);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  return BPMF_OK;
+}
+
+int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, cudaStream_t st) {
+  spd_check_kernel<<<1, 512, 0, st>>>(A, K, scratch, status);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  return BPMF_OK;
+}
+
+int launch_hyper_to_f32(Handle* h, int s) {
+  SideDev& sd = h->side[s];
+  hyper_f32<<<1, 256, 0, h->stream>>>(sd.lam, sd.mu, h->K, sd.lamf, sd.b0f);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  return BPMF_OK;
+}
+
+}  // namespace gb

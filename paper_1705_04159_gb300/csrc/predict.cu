@@ -1,0 +1,127 @@
+// predict.cu -- test predictions (Algorithm 1, "for all test points:
+// predict rating and compute RMSE").
+//
+// r_hat = u_row . v_col + mean.  One warp per pair reads both factor rows
+// coalesced and reduces with shuffles.  The registered test set is sorted by
+// user at registration so consecutive warps reuse the same user row.  Squared
+// errors of the latest sample and of the running mean of predictions are
+// reduced per block in FP64 and combined in block order (deterministic).
+#include <cuda_runtime.h>
+
+#include "bpmf_impl.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kPredThreads = 256;
+constexpr int kPredWarps = kPredThreads / 32;
+
+__device__ __forceinline__ float warp_dot(const float* __restrict__ u, const float* __restrict__ v,
+                                          int K, int lane) {
+  float s = 0.f;
+  for (int k = lane; k < K; k += 32) s = fmaf(__ldg(u + k), __ldg(v + k), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__global__ void predict_pairs(const float* __restrict__ U, const float* __restrict__ V, int K,
+                              double mean, const int32_t* __restrict__ row,
+                              const int32_t* __restrict__ col, int64_t n, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (int64_t)blockIdx.x * kPredWarps + (threadIdx.x >> 5);
+  for (int64_t p = w0; p < n; p += (int64_t)gridDim.x * kPredWarps) {
+    const float s = warp_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K, lane);
+    if (lane == 0) out[p] = (float)((double)s + mean);
+  }
+}
+
+__global__ void test_errors(const float* __restrict__ U, const float* __restrict__ V, int K,
+                            double mean, const int32_t* __restrict__ row,
+                            const int32_t* __restrict__ col, const float* __restrict__ truth,
+                            int64_t n, double* __restrict__ sum, int accumulate, double inv_avg,
+                            double* __restrict__ part) {
+  __shared__ double es[kPredWarps], em[kPredWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double e1 = 0.0, e2 = 0.0;
+  const int64_t w0 = (int64_t)blockIdx.x * kPredWarps + warp;
+  for (int64_t p = w0; p < n; p += (int64_t)gridDim.x * kPredWarps) {
+    const float s = warp_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K, lane);
+    if (lane == 0) {
+      const double pred = (double)s + mean;
+      const double d = pred - (double)truth[p];
+      e1 += d * d;
+      double acc = sum[p];
+      if (accumulate) {
+        acc += pred;
+        sum[p] = acc;
+      }
+      const double dm = acc * inv_avg - (double)truth[p];
+      e2 += dm * dm;
+    }
+  }
+  if (lane == 0) {
+    es[warp] = e1;
+    em[warp] = e2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kPredWarps; ++w) {
+      a += es[w];
+      b += em[w];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void test_final(const double* __restrict__ part, int blocks, int64_t n,
+                           double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < blocks; ++i) {
+      a += part[2 * i];
+      b += part[2 * i + 1];
+    }
+    out[0] = n > 0 ? sqrt(a / (double)n) : 0.0;
+    out[1] = n > 0 ? sqrt(b / (double)n) : 0.0;
+  }
+}
+
+int pred_blocks(Handle* h, int64_t n) {
+  int64_t b = (n + kPredWarps - 1) / kPredWarps;
+  const int64_t cap = 8LL * h->num_sms;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int launch_predict(Handle* h, int64_t n, const int32_t* r, const int32_t* c, float* out) {
+  if (n <= 0) return BPMF_OK;
+  h->kernels += 1;
+  predict_pairs<<<pred_blocks(h, n), kPredThreads, 0, h->stream>>>(
+      h->side[BPMF_USERS].X, h->side[BPMF_MOVIES].X, h->K, h->mean, r, c, n, out);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  return BPMF_OK;
+}
+
+int launch_test_step(Handle* h, bool accumulate) {
+  if (h->n_test <= 0) return BPMF_OK;
+  if (accumulate) h->n_avg += 1;
+  const double inv = h->n_avg > 0 ? 1.0 / (double)h->n_avg : 0.0;
+  const int blocks = pred_blocks(h, h->n_test);
+  PhaseTimer timer(h, BPMF_T_PREDICT);
+  h->kernels += 2;
+  test_errors<<<blocks, kPredThreads, 0, h->stream>>>(
+      h->side[BPMF_USERS].X, h->side[BPMF_MOVIES].X, h->K, h->mean, h->trow, h->tcol, h->tval,
+      h->n_test, h->tsum, accumulate ? 1 : 0, inv, h->red);
+  test_final<<<1, 32, 0, h->stream>>>(h->red, blocks, h->n_test, h->terr);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  h->have_rmse = true;
+  return BPMF_OK;
+}
+
+}  // namespace gb

@@ -1,0 +1,97 @@
+"""The C ABI library loads and exports every entry point include/bpmf.h declares.
+
+These run without a GPU: the library is built with nvcc for sm_103a and loaded
+with ctypes; only calls that fail argument checks before touching the device
+are made.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bpmf.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"BPMF_API\s+[\w\s\*]*?\b(bpmf_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    import paper_1705_04159_gb300 as bp
+    return bp.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("bpmf_init", "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict",
+                 "bpmf_get_state", "bpmf_set_state", "bpmf_destroy", "bpmf_strerror"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s+(\w+)$", out, flags=re.M))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    # nothing but the ABI is exported
+    extra = [n for n in exported if n.startswith("bpmf") and n not in _declared()]
+    assert not extra
+    lib = C.CDLL(libpath)
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_python_binding_names_match_abi(libpath):
+    import paper_1705_04159_gb300 as bp
+    for n in _declared():
+        if n in ("bpmf_last_error",):
+            continue
+        assert hasattr(bp, n), n
+
+
+def test_status_strings_and_defaults(libpath):
+    import paper_1705_04159_gb300 as bp
+    assert bp.bpmf_strerror(0) == "ok"
+    assert "invalid" in bp.bpmf_strerror(-1)
+    cfg = bp.bpmf_config_default(16)
+    assert cfg.K == 16 and cfg.nu0 == 16.0 and cfg.path == bp.PATH_MIXED
+    assert cfg.light_max == -1 and cfg.hub_min == -1
+
+
+@pytest.mark.parametrize("K", [0, 129])
+def test_init_rejects_bad_K_before_touching_the_device(libpath, K):
+    import numpy as np
+    import paper_1705_04159_gb300 as bp
+    cfg = bp.bpmf_config_default(max(K, 1))
+    cfg.K = K
+    with pytest.raises(bp.BpmfError) as e:
+        bp.bpmf_init(4, 4, np.zeros(1, np.int32), np.zeros(1, np.int32), np.ones(1, np.float32),
+                     cfg, stream=0)
+    assert e.value.code == bp.EINVAL
+
+
+def test_init_rejects_bad_prior(libpath):
+    import numpy as np
+    import paper_1705_04159_gb300 as bp
+    cfg = bp.bpmf_config_default(4)
+    cfg.nu0 = 2.0  # must exceed K - 1
+    with pytest.raises(bp.BpmfError) as e:
+        bp.bpmf_init(4, 4, np.zeros(1, np.int32), np.zeros(1, np.int32), np.ones(1, np.float32),
+                     cfg, stream=0)
+    assert e.value.code == bp.EINVAL
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1705_04159_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "bpmf_oracle" not in txt, f
