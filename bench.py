@@ -161,7 +161,13 @@ class ClockSampler:
 # ------------------------------------------------------------- workload --
 
 def load_workload(name, seed, device):
+    """A named recipe of synth, or "powerlaw:M:N:nnz:K:row_expo:col_expo"."""
     import synth
+    if name.startswith("powerlaw:"):
+        M, N, nnz, K = (int(x) for x in name.split(":")[1:5])
+        re_, ce = (float(x) for x in name.split(":")[5:7])
+        return synth.powerlaw(M, N, nnz, K, re_, ce, seed=seed, alpha=2.0, device=device,
+                              name=name)
     cache = os.environ.get("BPMF_SYNTH_CACHE", "/tmp/bpmf_synth_cache")
     return synth.make(name, seed=seed, device=device, cache_dir=cache)
 

@@ -52,7 +52,8 @@ void free_handle(Handle* h) {
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhl);
-    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamf); dfree(sd.b0f); dfree(sd.xbar); dfree(sd.S);
+    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.xbar); dfree(sd.S);
+    dfree(sd.piece_row); dfree(sd.piece_e0); dfree(sd.piece_e1); dfree(sd.hub_piece0);
   }
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
   dfree(h->flag_rows); dfree(h->flag_count); dfree(h->trow); dfree(h->tcol); dfree(h->tval);
@@ -202,8 +203,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       if ((rc = dalloc(&sd.X, sd.R * K))) break;
       if ((rc = dalloc(&sd.lam, KK))) break;
       if ((rc = dalloc(&sd.mu, K))) break;
-      if ((rc = dalloc(&sd.lamf, KK))) break;
-      if ((rc = dalloc(&sd.b0f, K))) break;
+      if ((rc = dalloc(&sd.lamaug, (int64_t)(K + 1) * (K + 1)))) break;
       if ((rc = dalloc(&sd.xbar, K))) break;
       if ((rc = dalloc(&sd.S, KK))) break;
     }

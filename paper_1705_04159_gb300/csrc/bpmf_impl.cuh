@@ -45,8 +45,13 @@ struct SideDev {
   uint32_t* Xhl = nullptr; // R*K packed (bf16 hi | bf16 lo << 16), mixed path only
   double* lam = nullptr;   // K*K
   double* mu = nullptr;    // K
-  float* lamf = nullptr;   // K*K
-  float* b0f = nullptr;    // K
+  float* lamaug = nullptr; // (K+1)^2: Lambda_s bordered by b0 = Lambda_s mu_s (row and column K)
+  // split rows (hubs): pieces of at most kPiece ratings, in degree order
+  int64_t n_hub = 0, n_pieces = 0;
+  int32_t* piece_row = nullptr;     // [n_pieces] row id
+  int64_t* piece_e0 = nullptr;      // [n_pieces] first rating
+  int64_t* piece_e1 = nullptr;      // [n_pieces] one past the last rating
+  int32_t* hub_piece0 = nullptr;    // [n_hub + 1] first piece of each hub (degree order)
   double* xbar = nullptr;  // K      (last statistics)
   double* S = nullptr;     // K*K
   int64_t bin_count[kNumBins] = {0, 0, 0, 0};  // rows per bin (perm order: hub, heavy, light, tiny)

@@ -260,6 +260,22 @@ __device__ void cta_bartlett(const double* C, double* A, double* B, double* Lam,
   __syncthreads();
 }
 
+// FP32 copy of Lambda bordered by b0 = Lambda mu: the (K+1) x (K+1) matrix
+// [[Lambda, b0], [b0^T, 0]] that the row kernels add alpha times the
+// rating-augmented Gram to.
+__device__ void write_bordered(const double* lam, const double* mu, int K, float* out) {
+  const int KA = K + 1;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) out[(e / K) * KA + (e % K)] = (float)lam[e];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += lam[i * K + k] * mu[k];
+    out[K * KA + i] = (float)s;
+    out[i * KA + K] = (float)s;
+  }
+  if (threadIdx.x == 0) out[K * KA + K] = 0.f;
+  __syncthreads();
+}
+
 struct HyperArgs {
   const double* xbar;
   const double* S;
@@ -274,8 +290,7 @@ struct HyperArgs {
   double* scr;  // 6 K*K + 2 K doubles
   double* lam;
   double* mu;
-  float* lamf;
-  float* b0f;
+  float* lamaug;
   int* status;
 };
 
@@ -329,12 +344,7 @@ __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
     for (int i = 0; i < K; ++i) a.mu[i] = mus[i] + x[i];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) a.lamf[e] = (float)a.lam[e];
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += a.lam[i * K + k] * a.mu[k];
-    a.b0f[i] = (float)s;
-  }
+  write_bordered(a.lam, a.mu, K, a.lamaug);
 }
 
 // Ainv = A^-1 for SPD A (used once for W0^-1); flags kStatusNotPD.
@@ -363,13 +373,8 @@ __global__ void __launch_bounds__(512) spd_check_kernel(const double* A, int K, 
 }
 
 // float copies of a side's hyperparameters (after bpmf_set_state)
-__global__ void hyper_f32(const double* lam, const double* mu, int K, float* lamf, float* b0f) {
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) lamf[e] = (float)lam[e];
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += lam[i * K + k] * mu[k];
-    b0f[i] = (float)s;
-  }
+__global__ void hyper_f32(const double* lam, const double* mu, int K, float* lamaug) {
+  write_bordered(lam, mu, K, lamaug);
 }
 
 template <int TM>
@@ -418,8 +423,7 @@ int launch_hyper(Handle* h, int s) {
   a.scr = h->wscr;
   a.lam = sd.lam;
   a.mu = sd.mu;
-  a.lamf = sd.lamf;
-  a.b0f = sd.b0f;
+  a.lamaug = sd.lamaug;
   a.status = h->status;
   {
     PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
@@ -447,7 +451,7 @@ int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, c
 
 int launch_hyper_to_f32(Handle* h, int s) {
   SideDev& sd = h->side[s];
-  hyper_f32<<<1, 256, 0, h->stream>>>(sd.lam, sd.mu, h->K, sd.lamf, sd.b0f);
+  hyper_f32<<<1, 256, 0, h->stream>>>(sd.lam, sd.mu, h->K, sd.lamaug);
   BPMF_CUDA_CHECK(cudaGetLastError());
   return BPMF_OK;
 }

@@ -1,279 +1,202 @@
 // rows.cu -- per-row conditional draws of one side (Algorithm 1's "update
 // movie m / user u based on the ratings for it and the model of the other
-// side, plus randomly sampled noise"), the FP64 redo of rows whose FP32
-// pivot fails, and the initial factors.
+// side, plus randomly sampled noise") on the FP32 CUDA cores, the partial
+// Grams of split rows, the FP64 redo of rows whose FP32 pivot fails, and the
+// initial factors.
 //
 // For row i with rated neighbours j (rows of the other side, factors v_j)
 // and centred ratings r_ij:
 //   Lambda* = Lambda_s + alpha sum_j v_j v_j^T      (K x K, SPD)
 //   b       = Lambda_s mu_s + alpha sum_j r_ij v_j
 //   L = chol(Lambda*) (lower), y = L^-1 b, u_i = L^-T (y + z)
-// with z the K Philox normals of (seed, iteration, side, i).  u_i then has
-// mean Lambda*^-1 b and covariance Lambda*^-1.  Rows of one side are
-// independent given the other side (paper Sec. III), so every row is a unit
-// of parallel work.
+// with z the K Philox normals of (seed, iteration, side, i).  u_i has mean
+// Lambda*^-1 b and covariance Lambda*^-1.  Rows of one side are independent
+// given the other side (paper Sec. III), so every row is a unit of work.
+//
+// Gram: each staged neighbour row carries its rating as feature K, so one
+// symmetric Gram of the (K+1)-vectors x_j = [v_j, r_ij] gives both
+// sum v_j v_j^T and sum r_ij v_j (its last row).  Rows are staged 32 at a
+// time in shared memory with cp.async, double-buffered, and accumulated in
+// FP32 register tiles (tile_chol.cuh); the same tiles then hold the bordered
+// matrix through the Cholesky.
 #include <cuda_runtime.h>
-#include <float.h>
 
 #include <algorithm>
 
 #include "bpmf_impl.cuh"
 #include "rows.cuh"
+#include "tile_chol.cuh"
 
 namespace gb {
 namespace {
 
-// A pivot below this fraction of its column's original diagonal means the
-// FP32 factorisation lost too many digits in that column: redo in FP64.
-constexpr float kPivotRel = 1e-4f;
-
-// Lower-triangular tile id t (0..135) of a 16 x 16 tile grid -> (ty, tx), ty >= tx.
-__device__ __forceinline__ void tri_tile(int t, int& ty, int& tx) {
-  int y = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while ((y + 1) * (y + 2) / 2 <= t) ++y;
-  while (y * (y + 1) / 2 > t) --y;
-  ty = y;
-  tx = t - y * (y + 1) / 2;
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
-
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
-__device__ __forceinline__ float pick(const float (&v)[N], int i) {
-  float r = v[0];
-#pragma unroll
-  for (int q = 1; q < N; ++q)
-    if (q == i) r = v[q];
-  return r;
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-template <int N>
-__device__ __forceinline__ void put(float (&v)[N], int i, float x) {
-#pragma unroll
-  for (int q = 0; q < N; ++q)
-    if (q == i) v[q] = x;
-}
-
-}  // namespace
-
-// Shared-memory floats of row_cta<TM>.
-__host__ __device__ constexpr int row_cta_smem_floats(int TM) {
-  // union{ staged rows 2*CH*KP + ratings 2*CH + ids 2*CH ; L columns KP*(KP+1) }
-  // + broadcast columns 2*KP + b, z, diag0 (3*KP)
-  return ((2 * 32 * 16 * TM + 4 * 32) > (16 * TM * (16 * TM + 1)) ? (2 * 32 * 16 * TM + 4 * 32)
-                                                                    : (16 * TM * (16 * TM + 1))) +
-         5 * 16 * TM;
-}
-
-// One CTA (256 threads) per row; K <= KP = 16 TM.
-//
-// Gram: neighbour rows are staged 32 at a time in shared memory; the 136
-// lower tiles (TM x TM each) of the KP x KP Gram are accumulated in FP32
-// registers by threads 0..135.  Cholesky: the tiles stay in registers; at
-// step k the owners of column k publish it through shared memory and every
-// tile applies the rank-one Schur update of its part of the trailing block.
-// The unscaled columns are kept in shared memory for the two triangular
-// solves, done by warp 0 with one row per lane.
-template <int TM>
-__global__ void __launch_bounds__(256) row_cta(const SweepArgs a) {
-  constexpr int KP = 16 * TM;
-  constexpr int CH = 32;
-  constexpr int LDS = KP + 1;
-  extern __shared__ float smem[];
-  float* Vs = smem;                         // [CH][KP] staged neighbour rows
-  float* rs = Vs + CH * KP;                 // [CH] ratings
-  int* nb = reinterpret_cast<int*>(rs + CH);  // [CH] neighbour ids
-  float* Lr = smem;                         // [KP][LDS] unscaled Cholesky columns (aliases)
-  float* tail = smem + row_cta_smem_floats(TM) - 5 * KP;
-  float* col = tail;                        // [2][KP]
-  float* bvec = col + 2 * KP;               // [KP]
-  float* zvec = bvec + KP;                  // [KP]
-  float* diag0 = zvec + KP;                 // [KP]
-  __shared__ int fail;
-
-  const int tid = threadIdx.x;
-  const int K = a.K;
-  const int64_t slot = a.row_begin + blockIdx.x;
-  if (slot >= a.row_end) return;
-  const int row = a.rows ? a.rows[slot] : (int)slot;
-  const int64_t p0 = a.ptr[row], p1 = a.ptr[row + 1];
-
-  const bool active = tid < 136;
-  int ty = 0, tx = 0;
-  if (active) tri_tile(tid, ty, tx);
-
-  if (tid == 0) fail = 0;
-  // normals of this row
-  if (tid * 4 < K) {
-    const float4 z = normal4_f32(philox(make_uint4((uint32_t)row, a.t, (uint32_t)tid, a.sw), a.key));
-    zvec[4 * tid] = z.x;
-    if (4 * tid + 1 < KP) zvec[4 * tid + 1] = z.y;
-    if (4 * tid + 2 < KP) zvec[4 * tid + 2] = z.z;
-    if (4 * tid + 3 < KP) zvec[4 * tid + 3] = z.w;
+// Stages neighbour rows [e0, e0 + cnt) as (K+1)-vectors [v_j, r] at stride KPs.
+__device__ __forceinline__ void stage_rows(const SweepArgs& a, int KPs, float* dst, int64_t e0,
+                                           int cnt) {
+  const int K = a.K, nt = blockDim.x;
+  if ((K & 3) == 0) {
+    const int Q = K >> 2;
+    for (int e = threadIdx.x; e < cnt * Q; e += nt) {
+      const int rr = e / Q, q = e - rr * Q;
+      const int64_t j = a.idx[e0 + rr];
+      cp_async16(dst + rr * KPs + 4 * q, a.Vo + j * K + 4 * q);
+    }
+  } else {
+    for (int e = threadIdx.x; e < cnt * K; e += nt) {
+      const int rr = e / K, k = e - rr * K;
+      const int64_t j = a.idx[e0 + rr];
+      cp_async4(dst + rr * KPs + k, a.Vo + j * K + k);
+    }
   }
-  // zero the padding columns of the staging buffer once
-  if (KP > K)
-    for (int e = tid; e < CH * KP; e += 256)
-      if (e % KP >= K) Vs[e] = 0.f;
+  for (int rr = threadIdx.x; rr < cnt; rr += nt) cp_async4(dst + rr * KPs + K, a.val + e0 + rr);
+  cp_async_commit();
+}
 
-  float acc[TM][TM];
-#pragma unroll
-  for (int p = 0; p < TM; ++p)
-#pragma unroll
-    for (int q = 0; q < TM; ++q) acc[p][q] = 0.f;
-  float hacc = 0.f;
-
-  for (int64_t c0 = p0; c0 < p1; c0 += CH) {
-    const int cnt = (int)min((int64_t)CH, p1 - c0);
-    __syncthreads();
-    if (tid < cnt) {
-      nb[tid] = a.idx[c0 + tid];
-      rs[tid] = a.val[c0 + tid];
-    }
-    __syncthreads();
-    if ((K & 3) == 0) {
-      const int K4 = K >> 2;
-      for (int e = tid; e < cnt * K4; e += 256) {
-        const int rr = e / K4, k4 = e - rr * K4;
-        const float4 v = __ldg(reinterpret_cast<const float4*>(a.Vo + (int64_t)nb[rr] * K) + k4);
-        float* d = Vs + rr * KP + 4 * k4;
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-      }
+// acc += sum over ratings [e0, e1) of x_j x_j^T (lower tiles, FP32).
+template <int TM>
+__device__ __forceinline__ void gram_gather(const SweepArgs& a, const TileGeom& G, float* Vs,
+                                            int64_t e0, int64_t e1, bool active, int ty, int tx,
+                                            float (&acc)[TM][TM]) {
+  const int KPs = G.KPs;
+  const int buf_floats = kChunk * KPs;
+  // padding columns K+1 .. KPs-1 stay zero (cp.async writes columns 0..K only)
+  for (int e = threadIdx.x; e < 2 * buf_floats; e += blockDim.x)
+    if (e % KPs > a.K) Vs[e] = 0.f;
+  const int64_t n = e1 - e0;
+  const int64_t nch = (n + kChunk - 1) / kChunk;
+  if (nch > 0) stage_rows(a, KPs, Vs, e0, (int)(n < kChunk ? n : kChunk));
+  for (int64_t c = 0; c < nch; ++c) {
+    if (c + 1 < nch) {
+      const int64_t s0 = e0 + (c + 1) * kChunk;
+      stage_rows(a, KPs, Vs + ((c + 1) & 1) * buf_floats, s0, (int)(e1 - s0 < kChunk ? e1 - s0 : kChunk));
+      cp_async_wait<1>();
     } else {
-      for (int e = tid; e < cnt * K; e += 256) {
-        const int rr = e / K, k = e - rr * K;
-        Vs[rr * KP + k] = __ldg(a.Vo + (int64_t)nb[rr] * K + k);
-      }
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const int cnt = (int)(n - c * kChunk < kChunk ? n - c * kChunk : kChunk);
+    const float* B = Vs + (c & 1) * buf_floats;
     if (active) {
       for (int rr = 0; rr < cnt; ++rr) {
         float va[TM], vb[TM];
-#pragma unroll
-        for (int q = 0; q < TM; ++q) {
-          va[q] = Vs[rr * KP + ty * TM + q];
-          vb[q] = Vs[rr * KP + tx * TM + q];
-        }
+        lds_vec<TM>(B + rr * KPs + ty * TM, va);
+        lds_vec<TM>(B + rr * KPs + tx * TM, vb);
 #pragma unroll
         for (int p = 0; p < TM; ++p)
 #pragma unroll
           for (int q = 0; q < TM; ++q) acc[p][q] = fmaf(va[p], vb[q], acc[p][q]);
       }
     }
-    if (tid < K)
-      for (int rr = 0; rr < cnt; ++rr) hacc = fmaf(rs[rr], Vs[rr * KP + tid], hacc);
-  }
-
-  // Lambda* = Lambda_s + alpha G (lower tiles), b = b0 + alpha h
-  if (active) {
-#pragma unroll
-    for (int p = 0; p < TM; ++p)
-#pragma unroll
-      for (int q = 0; q < TM; ++q) {
-        const int i = ty * TM + p, j = tx * TM + q;
-        float v = 0.f;
-        if (i < K && j <= i) v = fmaf(a.alpha, acc[p][q], __ldg(a.lamf + i * K + j));
-        acc[p][q] = v;
-        if (i == j && i < K) diag0[i] = v;
-      }
-  }
-  if (tid < K) bvec[tid] = fmaf(a.alpha, hacc, __ldg(a.b0f + tid));
-  __syncthreads();  // staging buffer is dead from here on; Lr reuses it
-
-  for (int k = 0; k < K; ++k) {
-    float* cb = col + (k & 1) * KP;
-    const int kt = k / TM, kq = k - kt * TM;
-    if (active && tx == kt) {
-#pragma unroll
-      for (int p = 0; p < TM; ++p) {
-        const int i = ty * TM + p;
-        if (i >= k && i < K) {
-          const float v = pick(acc[p], kq);
-          cb[i] = v;
-          Lr[i * LDS + k] = v;
-        }
-      }
-    }
     __syncthreads();
-    float piv = cb[k];
-    if (!(piv > kPivotRel * diag0[k])) {
-      if (tid == 0) fail = 1;
-      piv = fmaxf(fabsf(piv), FLT_MIN) + diag0[k] * kPivotRel;
-    }
-    if (active && (ty + 1) * TM > k + 1) {
-      const float rp = 1.0f / piv;
-      float ci[TM], cj[TM];
+  }
+}
+
+struct Smem {
+  float* Vs;
+  float* Lr;
+  float* cb;
+  float* zv;
+  float* diag0;
+  float* rinv;
+};
+
+__device__ __forceinline__ Smem carve(float* smem, const TileGeom& G) {
+  Smem s;
+  s.Vs = smem;
+  s.Lr = smem;
+  s.cb = smem + G.union_floats(2 * kChunk * G.KPs);
+  s.zv = s.cb + 2 * G.KP;
+  s.diag0 = s.zv + G.KP;
+  s.rinv = s.diag0 + G.KP;
+  return s;
+}
+
+int smem_bytes_fp32(const TileGeom& G) {
+  return (int)sizeof(float) * (G.union_floats(2 * kChunk * G.KPs) + G.tail_floats());
+}
+
+}  // namespace
+
+// Whole rows (mode 0) or hub rows from their partial Grams (mode 1).
+template <int TM>
+__global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int fail_sh;
+  const TileGeom G(a.K, TM);
+  const int64_t slot = a.row_begin + blockIdx.x;
+  if (slot >= a.row_end) return;
+  const int row = a.rows ? a.rows[slot] : (int)slot;
+  const Smem s = carve(smem, G);
+  const int tid = threadIdx.x;
+  const bool active = tid < G.ntiles;
+  int ty = 0, tx = 0;
+  if (active) tri_tile(tid, ty, tx);
+  if (tid == 0) fail_sh = 0;
+  for (int e = tid; e < 2 * G.KP; e += blockDim.x) s.cb[e] = 0.f;
+  row_normals(s.zv, a.K, row, a.t, a.sw, a.key);
+
+  float acc[TM][TM];
 #pragma unroll
-      for (int q = 0; q < TM; ++q) {
-        ci[q] = cb[ty * TM + q];
-        cj[q] = cb[tx * TM + q] * rp;
-      }
+  for (int p = 0; p < TM; ++p)
+#pragma unroll
+    for (int q = 0; q < TM; ++q) acc[p][q] = 0.f;
+
+  if (mode == 0) {
+    gram_gather<TM>(a, G, s.Vs, a.ptr[row], a.ptr[row + 1], active, ty, tx, acc);
+  } else if (active) {
+    const int32_t pb = a.hub_piece0[slot], pe = a.hub_piece0[slot + 1];
+    for (int32_t pc = pb; pc < pe; ++pc) {
+      const float* src = a.part + ((int64_t)pc * G.ntiles + tid) * (TM * TM);
 #pragma unroll
       for (int p = 0; p < TM; ++p)
 #pragma unroll
-        for (int q = 0; q < TM; ++q) {
-          const int i = ty * TM + p, j = tx * TM + q;
-          if (j > k && j <= i && i < K) acc[p][q] = fmaf(-ci[p], cj[q], acc[p][q]);
-        }
+        for (int q = 0; q < TM; ++q) acc[p][q] += __ldcs(src + p * TM + q);
     }
   }
+  form_bordered<TM>(acc, active, ty, tx, G, a.lamaug, a.alpha, s.diag0);
   __syncthreads();
-
-  if (fail) {
-    if (tid == 0) {
-      const int f = atomicAdd(a.flag_count, 1);
-      a.flag_rows[f] = row;
-    }
-    return;
+  if (!chol_solve_write<TM>(acc, active, ty, tx, G, s.Lr, s.cb, s.zv, s.diag0, s.rinv, &fail_sh,
+                            a.X + (int64_t)row * a.K)) {
+    if (tid == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
   }
+}
 
-  // L[k][k] = sqrt(Lr[k][k]), L[i][k] = Lr[i][k] / L[k][k]
-  if (tid < 32) {
-    constexpr int MW = (KP + 31) / 32;
-    const int lane = tid;
-    float w[MW], rinv[MW];
+// Partial Gram of one piece of a split row, stored as raw tiles.
+template <int TM>
+__global__ void __launch_bounds__(160) piece_fp32(const SweepArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const TileGeom G(a.K, TM);
+  const int64_t pc = blockIdx.x;
+  const int tid = threadIdx.x;
+  const bool active = tid < G.ntiles;
+  int ty = 0, tx = 0;
+  if (active) tri_tile(tid, ty, tx);
+  float acc[TM][TM];
 #pragma unroll
-    for (int m = 0; m < MW; ++m) {
-      const int i = lane + 32 * m;
-      const bool ok = i < K;
-      w[m] = ok ? bvec[i] : 0.f;
-      rinv[m] = ok ? 1.0f / sqrtf(Lr[i * LDS + i]) : 0.f;
-    }
-    // forward: y = L^-1 b
-    for (int k = 0; k < K; ++k) {
-      const int mk = k >> 5, lk = k & 31;
-      const float wk = __shfl_sync(0xffffffffu, pick(w, mk), lk);
-      const float rk = __shfl_sync(0xffffffffu, pick(rinv, mk), lk);
-      const float yk = wk * rk;
-      const float f = yk * rk;
+  for (int p = 0; p < TM; ++p)
 #pragma unroll
-      for (int m = 0; m < MW; ++m) {
-        const int i = lane + 32 * m;
-        if (i > k && i < K) w[m] = fmaf(-Lr[i * LDS + k], f, w[m]);
-      }
-      if (lane == lk) put(w, mk, yk);
-    }
+    for (int q = 0; q < TM; ++q) acc[p][q] = 0.f;
+  gram_gather<TM>(a, G, smem, a.piece_e0[pc], a.piece_e1[pc], active, ty, tx, acc);
+  if (active) {
+    float* dst = a.part + (pc * G.ntiles + tid) * (TM * TM);
 #pragma unroll
-    for (int m = 0; m < MW; ++m) {
-      const int i = lane + 32 * m;
-      if (i < K) w[m] += zvec[i];
-    }
-    // backward: x = L^-T (y + z)
-    for (int k = K - 1; k >= 0; --k) {
-      const int mk = k >> 5, lk = k & 31;
-      const float wk = __shfl_sync(0xffffffffu, pick(w, mk), lk);
-      const float rk = __shfl_sync(0xffffffffu, pick(rinv, mk), lk);
-      const float xk = wk * rk;
+    for (int p = 0; p < TM; ++p)
 #pragma unroll
-      for (int m = 0; m < MW; ++m) {
-        const int i = lane + 32 * m;
-        if (i < k) w[m] = fmaf(-Lr[k * LDS + i] * rinv[m], xk, w[m]);
-      }
-      if (lane == lk) put(w, mk, xk);
-    }
-#pragma unroll
-    for (int m = 0; m < MW; ++m) {
-      const int i = lane + 32 * m;
-      if (i < K) a.X[(int64_t)row * K + i] = w[m];
-    }
+      for (int q = 0; q < TM; ++q) dst[p * TM + q] = acc[p][q];
   }
 }
 
@@ -305,7 +228,8 @@ __global__ void __launch_bounds__(256) row_fp64(const SweepArgs a, const double*
     }
     for (int i = threadIdx.x; i < K; i += blockDim.x) {
       double s = 0.0, t = 0.0;
-      for (int64_t q = p0; q < p1; ++q) s += (double)a.val[q] * (double)a.Vo[(int64_t)a.idx[q] * K + i];
+      for (int64_t q = p0; q < p1; ++q)
+        s += (double)a.val[q] * (double)a.Vo[(int64_t)a.idx[q] * K + i];
       for (int k = 0; k < K; ++k) t += lam[i * K + k] * mu[k];
       b[i] = t + (double)a.alpha * s;
     }
@@ -363,49 +287,83 @@ __global__ void init_factors_kernel(float* X, int64_t R, int K, uint2 key, uint3
 
 namespace {
 
+int set_smem_attr(const void* fn, int bytes) {
+  BPMF_CUDA_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return BPMF_OK;
+}
+
 template <int TM>
-int launch_row_cta(const SweepArgs& a, int64_t nrows, cudaStream_t st, int64_t* launches) {
+int rows_fp32_tm(const SweepArgs& a, int mode, cudaStream_t st, int64_t* launches) {
+  const int64_t nrows = a.row_end - a.row_begin;
   if (nrows <= 0) return BPMF_OK;
-  const size_t smem = sizeof(float) * row_cta_smem_floats(TM);
-  static bool attr = false;
-  if (!attr) {
-    BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_cta<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-    attr = true;
-  }
+  const TileGeom G(a.K, TM);
+  const int smem = smem_bytes_fp32(G);
+  BPMF_TRY(set_smem_attr((const void*)row_fp32<TM>, smem));
   for (int64_t off = 0; off < nrows; off += 1LL << 30) {
     SweepArgs b = a;
     b.row_begin = a.row_begin + off;
-    const int64_t n = std::min<int64_t>(nrows - off, 1LL << 30);
-    b.row_end = b.row_begin + n;
-    row_cta<TM><<<(unsigned)n, 256, smem, st>>>(b);
+    b.row_end = b.row_begin + std::min<int64_t>(nrows - off, 1LL << 30);
+    row_fp32<TM><<<(unsigned)(b.row_end - b.row_begin), G.nthreads, smem, st>>>(b, mode);
     BPMF_CUDA_CHECK(cudaGetLastError());
     if (launches) *launches += 1;
   }
   return BPMF_OK;
 }
 
+template <int TM>
+int pieces_fp32_tm(const SweepArgs& a, int64_t npieces, cudaStream_t st, int64_t* launches) {
+  if (npieces <= 0) return BPMF_OK;
+  const TileGeom G(a.K, TM);
+  const int smem = (int)sizeof(float) * 2 * kChunk * G.KPs;
+  BPMF_TRY(set_smem_attr((const void*)piece_fp32<TM>, smem));
+  piece_fp32<TM><<<(unsigned)npieces, G.nthreads, smem, st>>>(a);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  if (launches) *launches += 1;
+  return BPMF_OK;
+}
+
 }  // namespace
 
-int launch_rows_cta(const SweepArgs& a, int64_t nrows, cudaStream_t st, int64_t* launches) {
-  if (a.K <= 16) return launch_row_cta<1>(a, nrows, st, launches);
-  if (a.K <= 32) return launch_row_cta<2>(a, nrows, st, launches);
-  if (a.K <= 64) return launch_row_cta<4>(a, nrows, st, launches);
-  if (a.K <= 112) return launch_row_cta<7>(a, nrows, st, launches);
-  return launch_row_cta<8>(a, nrows, st, launches);
+int64_t partial_floats_per_piece(int K) {
+  const int TM = tile_edge_for(K);
+  const TileGeom G(K, TM);
+  return (int64_t)G.ntiles * TM * TM;
+}
+
+int launch_rows_fp32(const SweepArgs& a, cudaStream_t st, int64_t* launches) {
+  switch (tile_edge_for(a.K)) {
+    case 2: return rows_fp32_tm<2>(a, 0, st, launches);
+    case 4: return rows_fp32_tm<4>(a, 0, st, launches);
+    default: return rows_fp32_tm<8>(a, 0, st, launches);
+  }
+}
+
+int launch_hub_finish_fp32(const SweepArgs& a, cudaStream_t st, int64_t* launches) {
+  switch (tile_edge_for(a.K)) {
+    case 2: return rows_fp32_tm<2>(a, 1, st, launches);
+    case 4: return rows_fp32_tm<4>(a, 1, st, launches);
+    default: return rows_fp32_tm<8>(a, 1, st, launches);
+  }
+}
+
+int launch_pieces_fp32(const SweepArgs& a, int64_t npieces, cudaStream_t st, int64_t* launches) {
+  switch (tile_edge_for(a.K)) {
+    case 2: return pieces_fp32_tm<2>(a, npieces, st, launches);
+    case 4: return pieces_fp32_tm<4>(a, npieces, st, launches);
+    default: return pieces_fp32_tm<8>(a, npieces, st, launches);
+  }
 }
 
 SweepArgs make_sweep_args(Handle* h, int s) {
   SideDev& sd = h->side[s];
   SideDev& od = h->side[1 - s];
-  SweepArgs a;
+  SweepArgs a{};
   a.ptr = sd.ptr;
   a.idx = sd.idx;
   a.val = sd.val;
   a.Vo = od.X;
   a.X = sd.X;
-  a.lamf = sd.lamf;
-  a.b0f = sd.b0f;
+  a.lamaug = sd.lamaug;
   a.rows = nullptr;
   a.row_begin = 0;
   a.row_end = sd.R;
@@ -416,31 +374,31 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.sw = stream_word(kStreamRow, s);
   a.flag_rows = h->flag_rows;
   a.flag_count = h->flag_count;
+  a.piece_row = sd.piece_row;
+  a.piece_e0 = sd.piece_e0;
+  a.piece_e1 = sd.piece_e1;
+  a.hub_piece0 = sd.hub_piece0;
+  a.part = h->hub_part;
   return a;
 }
 
 int launch_fp64_redo(Handle* h, int s, const SweepArgs& a) {
   const size_t smem = sizeof(double) * ((size_t)h->K * h->K + 2 * h->K);
-  static bool attr = false;
-  if (!attr) {
-    BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * (kMaxK * kMaxK + 2 * kMaxK))));
-    attr = true;
-  }
+  BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double) * (kMaxK * kMaxK + 2 * kMaxK))));
   row_fp64<<<h->num_sms, 256, smem, h->stream>>>(a, h->side[s].lam, h->side[s].mu, h->status);
   BPMF_CUDA_CHECK(cudaGetLastError());
   return BPMF_OK;
 }
 
 int launch_sweep(Handle* h, int s) {
-  SideDev& sd = h->side[s];
   cudaStream_t st = h->stream;
   BPMF_CUDA_CHECK(cudaMemsetAsync(h->flag_count, 0, sizeof(int32_t), st));
   SweepArgs a = make_sweep_args(h, s);
   {
     PhaseTimer timer(h, s == BPMF_USERS ? BPMF_T_ROWS_USERS : BPMF_T_ROWS_MOVIES);
     if (h->cfg.path == BPMF_PATH_PLAIN) {
-      BPMF_TRY(launch_rows_cta(a, sd.R, st, &h->kernels));
+      BPMF_TRY(launch_rows_fp32(a, st, &h->kernels));
     } else {
       BPMF_TRY(launch_sweep_binned(h, s, a));
     }

@@ -5,14 +5,16 @@
 
 namespace gb {
 
+constexpr int kChunk = 32;          // neighbour rows staged per pipeline step
+constexpr int64_t kPiece = 4096;    // ratings per piece of a split (hub) row
+
 struct SweepArgs {
   const int64_t* ptr;   // row pointers of this side
   const int32_t* idx;   // neighbour ids (rows of the other side)
   const float* val;     // centred ratings
   const float* Vo;      // other side's factors, ld K
   float* X;             // this side's factors (written), ld K
-  const float* lamf;    // Lambda_s, K*K float
-  const float* b0f;     // Lambda_s mu_s, K float
+  const float* lamaug;  // (K+1)^2 bordered [[Lambda_s, b0], [b0^T, 0]]
   const int32_t* rows;  // row list (degree order) or nullptr for 0..R-1
   int64_t row_begin, row_end;  // slice of the row list
   int K;
@@ -22,10 +24,23 @@ struct SweepArgs {
   uint32_t sw;          // stream word (ROW << 8 | side)
   int32_t* flag_rows;   // rows whose FP32 pivot failed
   int32_t* flag_count;
+  // split rows: piece p covers ratings [piece_e0[p], piece_e1[p]) of piece_row[p];
+  // hub h (slot h of the degree order) owns pieces [hub_piece0[h], hub_piece0[h+1])
+  const int32_t* piece_row;
+  const int64_t* piece_e0;
+  const int64_t* piece_e1;
+  const int32_t* hub_piece0;
+  float* part;          // partial Gram tiles [piece][tile][TM * TM]
 };
 
-int launch_rows_cta(const SweepArgs& a, int64_t nrows, cudaStream_t st, int64_t* launches);
-int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 SweepArgs make_sweep_args(Handle* h, int s);
+// whole rows row_begin..row_end of the row list, Gram from the ratings
+int launch_rows_fp32(const SweepArgs& a, cudaStream_t st, int64_t* launches);
+// partial Grams of pieces [0, npieces)
+int launch_pieces_fp32(const SweepArgs& a, int64_t npieces, cudaStream_t st, int64_t* launches);
+// hub rows row_begin..row_end (degree order) from their partial Grams
+int launch_hub_finish_fp32(const SweepArgs& a, cudaStream_t st, int64_t* launches);
+int64_t partial_floats_per_piece(int K);
+int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 
 }  // namespace gb

@@ -104,6 +104,26 @@ def test_sweep_parity(gpu_lib, name, path):
             assert np.array_equal(gV if side == 0 else gU, V if side == 0 else U)
 
 
+@pytest.mark.parametrize("name,hub_min", [("tiny_k10", 20), ("powerlaw_k64", 60),
+                                          ("powerlaw_k100", 90), ("uniform_k7", 16),
+                                          ("powerlaw_k128", 64)])
+def test_sweep_parity_split_hubs(gpu_lib, name, hub_min):
+    """Rows with degree >= hub_min are split into pieces of hub_min / 2
+    ratings whose partial Grams are summed in piece order."""
+    bp = gpu_lib
+    ds, K, st = _case(name)
+    U, V, hy, hyper = random_state(ds, K)
+    with _sampler(bp, ds, K, bp.PATH_BINNED, seed=13, hub_min=hub_min) as s:
+        for side in (0, 1):
+            bins, _ = s.sweep_info(side)
+            assert bins[3] > 0, "case must exercise split rows"
+            s.set_state(U, V, hyper, it=4)
+            s.sweep(side)
+            got = s.get_state()[side]
+            ref = oracle_sweep(ds, side, U, V, hy, ds.alpha, 13, 4, structure=st)
+            assert rel_err(got, ref).max() <= TAU_FP32
+
+
 def test_paths_agree_bitwise(gpu_lib):
     bp = gpu_lib
     ds, K, _ = _case("powerlaw_k64")
