@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],
+                   help="execution path of the main arm")
     p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     return p.parse_args()
 
@@ -335,9 +337,10 @@ def main():
     ds = load_workload(args.workload, args.seed, "cuda")
     K = ds.K
     work = algorithmic_work(ds, K)
+    main_path = {"mixed": bp.PATH_MIXED, "binned": bp.PATH_BINNED, "plain": bp.PATH_PLAIN}[args.path]
 
     with ClockSampler(local) as clk:
-        mixed = device_arm(bp, ds, bp.PATH_MIXED, args.steps, args.warmup, world, stream)
+        mixed = device_arm(bp, ds, main_path, args.steps, args.warmup, world, stream)
     clocks = clk.summary()
     ms = max_over_ranks(world, mixed["ms"])
     rows = ds.M + ds.N
@@ -354,7 +357,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e = e2e_arm(bp, ds, bp.PATH_MIXED, args.steps, stream)
+        e = e2e_arm(bp, ds, main_path, args.steps, stream)
         em = max_over_ranks(world, e["ms"])
         e2e = {"value": world * rows * args.steps / (em / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(e["h2d"]), "d2h_bytes_per_step": int(e["d2h"]),
@@ -387,7 +390,7 @@ def main():
             "data": "synthetic (seeded Netflix-shaped ratings generated on the device)",
             "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train + "
                                    f"{len(ds.test_row)} test ratings, K={K}",
-                       "path": "mixed", "global_batch": rows, "parallelism": f"replicas{world}",
+                       "path": args.path, "global_batch": rows, "parallelism": f"replicas{world}",
                        "l2": "no flush: per-iteration working set > 1.4 GB vs 129 MB L2"},
             "clocks": clocks, "gpu_launches": int(mixed["kernels"]),
             "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},

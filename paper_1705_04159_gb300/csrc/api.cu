@@ -93,6 +93,10 @@ int check_status(Handle* h, const char* where) {
     set_error("%s: index out of range", where);
     return BPMF_EINVAL;
   }
+  if (st & kStatusTimeout) {
+    set_error("%s: a tensor-core pipeline wait timed out", where);
+    return BPMF_ECUDA;
+  }
   return BPMF_OK;
 }
 

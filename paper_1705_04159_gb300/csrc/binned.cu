@@ -26,8 +26,10 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   cudaStream_t st = h->stream;
   SweepArgs a = a0;
   a.rows = sd.perm;
+  const bool tc = h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K);
   if (sd.n_hub > 0) {
-    BPMF_TRY(launch_pieces_fp32(a, sd.n_pieces, st, &h->kernels));
+    if (tc) BPMF_TRY(launch_pieces_tc(a, sd.n_pieces, h->status, st, &h->kernels));
+    else BPMF_TRY(launch_pieces_fp32(a, sd.n_pieces, st, &h->kernels));
     SweepArgs f = a;
     f.row_begin = 0;
     f.row_end = sd.n_hub;
@@ -35,6 +37,7 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   }
   a.row_begin = sd.n_hub;
   a.row_end = sd.R;
+  if (tc) return launch_rows_tc(a, h->status, st, &h->kernels);
   return launch_rows_fp32(a, st, &h->kernels);
 }
 

@@ -31,6 +31,7 @@ constexpr uint32_t kStreamInit = 4u;
 constexpr int kStatusNotPD = 1;
 constexpr int kStatusRng = 2;
 constexpr int kStatusIndex = 4;
+constexpr int kStatusTimeout = 8;  // a bounded wait on the tensor-core pipeline gave up
 
 // degree bins
 enum Bin { kBinTiny = 0, kBinLight = 1, kBinHeavy = 2, kBinHub = 3, kNumBins = 4 };

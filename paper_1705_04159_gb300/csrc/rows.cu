@@ -74,8 +74,11 @@ __device__ __forceinline__ void gram_gather(const SweepArgs& a, const TileGeom& 
   const int KPs = G.KPs;
   const int buf_floats = kChunk * KPs;
   // padding columns K+1 .. KPs-1 stay zero (cp.async writes columns 0..K only)
-  for (int e = threadIdx.x; e < 2 * buf_floats; e += blockDim.x)
-    if (e % KPs > a.K) Vs[e] = 0.f;
+  const int pad = KPs - (a.K + 1);
+  for (int e = threadIdx.x; e < 2 * kChunk * pad; e += blockDim.x) {
+    const int rr = e / pad;
+    Vs[rr * KPs + a.K + 1 + (e - rr * pad)] = 0.f;
+  }
   const int64_t n = e1 - e0;
   const int64_t nch = (n + kChunk - 1) / kChunk;
   if (nch > 0) stage_rows(a, KPs, Vs, e0, (int)(n < kChunk ? n : kChunk));
@@ -105,24 +108,9 @@ __device__ __forceinline__ void gram_gather(const SweepArgs& a, const TileGeom& 
   }
 }
 
-struct Smem {
-  float* Vs;
-  float* Lr;
-  float* cb;
-  float* zv;
-  float* diag0;
-  float* rinv;
-};
-
-__device__ __forceinline__ Smem carve(float* smem, const TileGeom& G) {
-  Smem s;
-  s.Vs = smem;
-  s.Lr = smem;
-  s.cb = smem + G.union_floats(2 * kChunk * G.KPs);
-  s.zv = s.cb + 2 * G.KP;
-  s.diag0 = s.zv + G.KP;
-  s.rinv = s.diag0 + G.KP;
-  return s;
+// staging buffers and L share the front of shared memory; the rest follows
+__device__ __forceinline__ CholSmem carve(float* smem, const TileGeom& G) {
+  return carve_chol(smem, smem + G.union_floats(2 * kChunk * G.KPs), G);
 }
 
 int smem_bytes_fp32(const TileGeom& G) {
@@ -140,13 +128,12 @@ __global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
   const int64_t slot = a.row_begin + blockIdx.x;
   if (slot >= a.row_end) return;
   const int row = a.rows ? a.rows[slot] : (int)slot;
-  const Smem s = carve(smem, G);
+  const CholSmem s = carve(smem, G);
   const int tid = threadIdx.x;
   const bool active = tid < G.ntiles;
   int ty = 0, tx = 0;
-  if (active) tri_tile(tid, ty, tx);
+  if (active) tri_tile(tid, G.g, ty, tx);
   if (tid == 0) fail_sh = 0;
-  for (int e = tid; e < 2 * G.KP; e += blockDim.x) s.cb[e] = 0.f;
   row_normals(s.zv, a.K, row, a.t, a.sw, a.key);
 
   float acc[TM][TM];
@@ -156,7 +143,7 @@ __global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
     for (int q = 0; q < TM; ++q) acc[p][q] = 0.f;
 
   if (mode == 0) {
-    gram_gather<TM>(a, G, s.Vs, a.ptr[row], a.ptr[row + 1], active, ty, tx, acc);
+    gram_gather<TM>(a, G, smem, a.ptr[row], a.ptr[row + 1], active, ty, tx, acc);
   } else if (active) {
     const int32_t pb = a.hub_piece0[slot], pe = a.hub_piece0[slot + 1];
     for (int32_t pc = pb; pc < pe; ++pc) {
@@ -169,8 +156,7 @@ __global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
   }
   form_bordered<TM>(acc, active, ty, tx, G, a.lamaug, a.alpha, s.diag0);
   __syncthreads();
-  if (!chol_solve_write<TM>(acc, active, ty, tx, G, s.Lr, s.cb, s.zv, s.diag0, s.rinv, &fail_sh,
-                            a.X + (int64_t)row * a.K)) {
+  if (!chol_solve_write<TM>(acc, active, ty, tx, G, s, &fail_sh, a.X + (int64_t)row * a.K)) {
     if (tid == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
   }
 }
@@ -184,7 +170,7 @@ __global__ void __launch_bounds__(160) piece_fp32(const SweepArgs a) {
   const int tid = threadIdx.x;
   const bool active = tid < G.ntiles;
   int ty = 0, tx = 0;
-  if (active) tri_tile(tid, ty, tx);
+  if (active) tri_tile(tid, G.g, ty, tx);
   float acc[TM][TM];
 #pragma unroll
   for (int p = 0; p < TM; ++p)

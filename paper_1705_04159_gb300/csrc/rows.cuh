@@ -41,6 +41,11 @@ int launch_pieces_fp32(const SweepArgs& a, int64_t npieces, cudaStream_t st, int
 // hub rows row_begin..row_end (degree order) from their partial Grams
 int launch_hub_finish_fp32(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 int64_t partial_floats_per_piece(int K);
+// tensor-core Gram (rows_tc.cu); supported for 48 <= K <= 119
+bool tc_supported(int K);
+int launch_rows_tc(const SweepArgs& a, int* status, cudaStream_t st, int64_t* launches);
+int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStream_t st,
+                     int64_t* launches);
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 
 }  // namespace gb

@@ -1,4 +1,4 @@
-// tile_chol.cuh -- register-tile Cholesky and solve shared by the row kernels.
+// tile_chol.cuh -- register-tile blocked Cholesky and solve shared by the row kernels.
 //
 // The row draw (Algorithm 1's row update) needs L = chol(Lambda*), y = L^-1 b
 // and u = L^-T (y + z).  The kernels factor the bordered matrix
@@ -9,13 +9,8 @@
 //
 // Layout: the lower triangle of the (K+1)-square matrix is cut into TM x TM
 // tiles on a g x g grid (g = ceil((K+1)/TM)); thread t < g(g+1)/2 owns tile
-// (ty, tx) with ty >= tx and keeps it in registers.  Step k of the
-// right-looking factorisation publishes column k through shared memory and
-// every tile with rows below k applies the rank-one Schur update
-//     A[i][j] -= A[i][k] A[j][k] / A[k][k]
-// to all its entries without predicates: entries of finished columns receive
-// harmless updates that are never read again, because each column is stored
-// (unscaled) in shared memory at the step that finishes it.
+// (ty, tx) with ty >= tx and keeps it in registers through the blocked
+// factorisation below (one panel per tile column).
 #pragma once
 
 #include <float.h>
@@ -49,17 +44,27 @@ struct TileGeom {
     const int u = stage_floats > lr ? stage_floats : lr;
     return (u + 3) & ~3;
   }
-  // floats after the union: broadcast columns (2 KP), z, diag0, 1/sqrt(pivot)
-  __host__ __device__ int tail_floats() const { return ((5 * KP) + 3) & ~3; }
+  // floats after the union: panel tiles, diagonal block, z, diag0, 1 / L_kk
+  __host__ __device__ int tail_floats() const {
+    return ((g * TM * TM + TM * TM + 3 * KP) + 3) & ~3;
+  }
 };
 
-// tile id t -> (ty, tx) with ty >= tx, t = ty (ty + 1) / 2 + tx
-__device__ __forceinline__ void tri_tile(int t, int& ty, int& tx) {
-  int y = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while ((y + 1) * (y + 2) / 2 <= t) ++y;
-  while (y * (y + 1) / 2 > t) --y;
-  ty = y;
-  tx = t - y * (y + 1) / 2;
+// Tile numbering from the bottom-right corner: t = u (u + 1) / 2 + v with
+// u = g - 1 - tx and v = ty - tx.  The trailing triangle of every panel
+// (tx > c) is then the prefix t < (g-1-c)(g-c)/2, so the threads that still
+// have work at panel c fill whole warps, and the panel's own column of tiles
+// is one contiguous run of thread ids.
+__device__ __forceinline__ void tri_tile(int t, int g, int& ty, int& tx) {
+  int u = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((u + 1) * (u + 2) / 2 <= t) ++u;
+  while (u * (u + 1) / 2 > t) --u;
+  tx = g - 1 - u;
+  ty = tx + (t - u * (u + 1) / 2);
+}
+__host__ __device__ __forceinline__ int tile_id(int ty, int tx, int g) {
+  const int u = g - 1 - tx;
+  return u * (u + 1) / 2 + (ty - tx);
 }
 
 template <int N>
@@ -126,84 +131,165 @@ __device__ __forceinline__ void form_bordered(float (&acc)[TM][TM], bool active,
     }
 }
 
-// Factorises the bordered tile matrix and writes u = L^-T (y + z) to xout.
-// Preconditions: acc formed by form_bordered, cb[0 .. 2 KP) zeroed, zv holds
-// the normals, the block is synchronised.  Returns false (on all threads) if
-// a pivot failed; xout is then not written.
+// u = L^-T (y + z) by one warp (lanes own rows i = lane + 32 m), where
+// L[i][j] = Lr[i * LDS + j] (scaled factor, lower triangle), y_i = L[K][i]
+// (the bordered row) and rinv[k] = 1 / L[k][k].  Column-oriented back
+// substitution: x_k = w_k / L_kk, then w_i -= L[k][i] x_k for i < k.
+__device__ __forceinline__ void backward_solve(const float* Lr, int LDS, int K, const float* rinv,
+                                               const float* zv, float* __restrict__ xout) {
+  constexpr int MW = kMaxK / 32;
+  const int lane = threadIdx.x & 31;
+  float w[MW];
+#pragma unroll
+  for (int m = 0; m < MW; ++m) {
+    const int i = lane + 32 * m;
+    w[m] = i < K ? Lr[K * LDS + i] + zv[i] : 0.f;
+  }
+  for (int k = K - 1; k >= 0; --k) {
+    const int mk = k >> 5, lk = k & 31;
+    const float wk = __shfl_sync(0xffffffffu, pick(w, mk), lk);
+    const float xk = wk * rinv[k];
+#pragma unroll
+    for (int m = 0; m < MW; ++m) {
+      const int i = lane + 32 * m;
+      if (i < k) w[m] = fmaf(-Lr[k * LDS + i], xk, w[m]);
+    }
+    if (lane == lk) put(w, mk, xk);
+  }
+#pragma unroll
+  for (int m = 0; m < MW; ++m) {
+    const int i = lane + 32 * m;
+    if (i < K) xout[i] = w[m];
+  }
+}
+
+// Shared memory of the factorisation: L (scaled, row stride LDS, lower
+// triangle plus the bordered row K), the panel tiles of the current panel
+// (column-major TM x TM per tile row), the factored diagonal block, the
+// normals, the starting diagonal and 1 / L_kk.
+struct CholSmem {
+  float* Lr;
+  float* pbuf;
+  float* lbuf;
+  float* zv;
+  float* diag0;
+  float* rinv;
+};
+
+__device__ __forceinline__ CholSmem carve_chol(float* Lr, float* tail, const TileGeom& G) {
+  CholSmem c;
+  c.Lr = Lr;
+  c.pbuf = tail;
+  c.lbuf = c.pbuf + G.g * G.TM * G.TM;
+  c.zv = c.lbuf + G.TM * G.TM;
+  c.diag0 = c.zv + G.KP;
+  c.rinv = c.diag0 + G.KP;
+  return c;
+}
+
+// Blocked right-looking Cholesky of the bordered tile matrix, then
+// u = L^-T (y + z) written to xout.  Panel c (pivot columns c TM .. c TM +
+// nc - 1, nc <= TM) takes three phases separated by two barriers:
+//   (1) the owner of diagonal tile (c, c) factors it in registers
+//       (rows past the pivot block, i.e. the bordered row K, are treated as
+//       rows below it) and publishes L11 and 1 / L_jj;
+//   (2) the owners of tiles (ty, c), ty > c, solve L21 = A21 L11^-T and
+//       publish their tiles column by column;
+//   (3) the owners of trailing tiles (ty, tx), ty >= tx > c, subtract
+//       L[ty][c] L[tx][c]^T as TM rank-one updates.
+// A panel is partial only when it also holds column K, and then it is the
+// last tile column, so trailing updates always see full panels.
+// Preconditions: acc formed by form_bordered, zv holds the normals, the block
+// is synchronised.  Returns false (on all threads) if a pivot failed; xout is
+// then not written.
 template <int TM>
 __device__ bool chol_solve_write(float (&acc)[TM][TM], bool active, int ty, int tx,
-                                 const TileGeom& G, float* Lr, float* cb, const float* zv,
-                                 const float* diag0, float* rinv, int* fail_sh,
+                                 const TileGeom& G, const CholSmem& cs, int* fail_sh,
                                  float* __restrict__ xout) {
-  const int K = G.K, KA = G.KA, KP = G.KP, LDS = G.LDS;
+  const int K = G.K, KA = G.KA, LDS = G.LDS;
+  const int gc = (K + TM - 1) / TM;
   const int tid = threadIdx.x;
-  for (int k = 0; k < K; ++k) {
-    float* cbk = cb + (k & 1) * KP;
-    const int kt = k / TM, kq = k - kt * TM;
-    if (active && tx == kt) {
+  for (int c = 0; c < gc; ++c) {
+    const int c0 = c * TM;
+    const int nc = K - c0 < TM ? K - c0 : TM;
+    if (active && ty == c && tx == c) {
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        if (j < nc) {
+          float piv = acc[j][j];
+          const float d0 = cs.diag0[c0 + j];
+          if (!(piv > kPivotRel * d0)) {
+            *fail_sh = 1;
+            piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+          }
+          const float d = sqrtf(piv);
+          const float rd = 1.0f / d;
+          acc[j][j] = d;
+          cs.rinv[c0 + j] = rd;
+#pragma unroll
+          for (int i = j + 1; i < TM; ++i) acc[i][j] *= rd;
+#pragma unroll
+          for (int i = j + 1; i < TM; ++i)
+#pragma unroll
+            for (int l = j + 1; l <= i; ++l) acc[i][l] = fmaf(-acc[i][j], acc[l][j], acc[i][l]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < TM; ++p)
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+          cs.lbuf[p * TM + q] = acc[p][q];
+          if (q < nc && q <= p && c0 + p < KA) cs.Lr[(c0 + p) * LDS + c0 + q] = acc[p][q];
+        }
+    }
+    __syncthreads();
+    if (active && tx == c && ty > c) {
+#pragma unroll
+      for (int j = 0; j < TM; ++j) {
+        if (j < nc) {
+          const float rj = cs.rinv[c0 + j];
+#pragma unroll
+          for (int p = 0; p < TM; ++p) {
+            float t = acc[p][j];
+#pragma unroll
+            for (int l = 0; l < j; ++l) t = fmaf(-acc[p][l], cs.lbuf[j * TM + l], t);
+            acc[p][j] = t * rj;
+          }
+        }
+      }
+      float* pb = cs.pbuf + ty * TM * TM;
+#pragma unroll
+      for (int l = 0; l < TM; ++l)
+#pragma unroll
+        for (int p = 0; p < TM; ++p) pb[l * TM + p] = acc[p][l];
 #pragma unroll
       for (int p = 0; p < TM; ++p) {
         const int i = ty * TM + p;
-        if (i >= k && i < KA) {
-          const float v = pick(acc[p], kq);
-          cbk[i] = v;
-          Lr[i * LDS + k] = v;
+        if (i < KA) {
+#pragma unroll
+          for (int q = 0; q < TM; ++q)
+            if (q < nc) cs.Lr[i * LDS + c0 + q] = acc[p][q];
         }
       }
     }
     __syncthreads();
-    float piv = cbk[k];
-    const float d0 = diag0[k];
-    if (!(piv > kPivotRel * d0)) {
-      if (tid == 0) *fail_sh = 1;
-      piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
-    }
-    if (active && (ty + 1) * TM > k + 1) {
-      const float rp = 1.0f / piv;
-      float ci[TM], cj[TM];
-      lds_vec<TM>(cbk + ty * TM, ci);
-      lds_vec<TM>(cbk + tx * TM, cj);
+    if (active && tx > c) {
+      const float* pi = cs.pbuf + ty * TM * TM;
+      const float* pj = cs.pbuf + tx * TM * TM;
 #pragma unroll
-      for (int q = 0; q < TM; ++q) cj[q] *= rp;
+      for (int l = 0; l < TM; ++l) {
+        float va[TM], vb[TM];
+        lds_vec<TM>(pi + l * TM, va);
+        lds_vec<TM>(pj + l * TM, vb);
 #pragma unroll
-      for (int p = 0; p < TM; ++p)
+        for (int p = 0; p < TM; ++p)
 #pragma unroll
-        for (int q = 0; q < TM; ++q) acc[p][q] = fmaf(-ci[p], cj[q], acc[p][q]);
-    }
-  }
-  __syncthreads();
-  if (*fail_sh) return false;
-  for (int k = tid; k < K; k += blockDim.x) rinv[k] = 1.0f / sqrtf(Lr[k * LDS + k]);
-  __syncthreads();
-  if (tid < 32) {
-    constexpr int MW = TM == 8 ? 4 : (TM == 4 ? 2 : 1);
-    const int lane = tid;
-    float w[MW], ri[MW];
-#pragma unroll
-    for (int m = 0; m < MW; ++m) {
-      const int i = lane + 32 * m;
-      const bool ok = i < K;
-      ri[m] = ok ? rinv[i] : 0.f;
-      // y_i = L[K][i] = Lr[K][i] / sqrt(pivot_i): the bordered row
-      w[m] = ok ? fmaf(Lr[K * LDS + i], ri[m], zv[i]) : 0.f;
-    }
-    for (int k = K - 1; k >= 0; --k) {
-      const int mk = k >> 5, lk = k & 31;
-      const float wk = __shfl_sync(0xffffffffu, pick(w, mk), lk);
-      const float xk = wk * rinv[k];
-#pragma unroll
-      for (int m = 0; m < MW; ++m) {
-        const int i = lane + 32 * m;
-        if (i < k) w[m] = fmaf(-Lr[k * LDS + i] * ri[m], xk, w[m]);
+          for (int q = 0; q < TM; ++q) acc[p][q] = fmaf(-va[p], vb[q], acc[p][q]);
       }
-      if (lane == lk) put(w, mk, xk);
-    }
-#pragma unroll
-    for (int m = 0; m < MW; ++m) {
-      const int i = lane + 32 * m;
-      if (i < K) xout[i] = w[m];
     }
   }
+  if (*fail_sh) return false;
+  if (tid < 32) backward_solve(cs.Lr, LDS, K, cs.rinv, cs.zv, xout);
   return true;
 }
 

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import (TAU_FP32, kappa_rows, oracle_structure, oracle_sweep, random_state,
+from parity_util import (TAU_BF16, TAU_FP32, kappa_rows, oracle_structure, oracle_sweep, random_state,
                          rel_err)
 
 pytestmark = pytest.mark.gpu
@@ -31,6 +31,8 @@ CASES = {
     "powerlaw_k33": (lambda: synth.powerlaw(1500, 400, 30000, 33, 0.5, 0.8, seed=6), 33),
     "powerlaw_k100": (lambda: synth.powerlaw(3000, 700, 80000, 100, 0.5, 0.9, seed=7), 100),
     "powerlaw_k128": (lambda: synth.powerlaw(1200, 300, 30000, 128, 0.5, 0.9, seed=8), 128),
+    "powerlaw_k55": (lambda: synth.powerlaw(1000, 400, 25000, 55, 0.5, 0.8, seed=9), 55),
+    "uniform_k119": (lambda: synth.uniform(400, 150, 12000, 119, seed=10), 119),
 }
 _cache = {}
 
@@ -122,6 +124,29 @@ def test_sweep_parity_split_hubs(gpu_lib, name, hub_min):
             got = s.get_state()[side]
             ref = oracle_sweep(ds, side, U, V, hy, ds.alpha, 13, 4, structure=st)
             assert rel_err(got, ref).max() <= TAU_FP32
+
+
+@pytest.mark.parametrize("name,hub_min", [("powerlaw_k64", -1), ("powerlaw_k100", -1),
+                                          ("powerlaw_k55", -1), ("uniform_k119", -1),
+                                          ("powerlaw_k100", 90), ("powerlaw_k64", 60)])
+def test_sweep_parity_tensor_gram(gpu_lib, name, hub_min):
+    """Mixed path: bf16 hi/lo tcgen05 Gram (hi.hi + hi.lo + lo.hi, FP32
+    accumulation in tensor memory), FP32 Cholesky.  The contract is the BF16
+    tolerance 1e-2; the split product is accurate to ~2^-16, so the observed
+    error must also stay far below it (1e-3), which a missing cross term
+    would break."""
+    bp = gpu_lib
+    ds, K, st = _case(name)
+    U, V, hy, hyper = random_state(ds, K)
+    with _sampler(bp, ds, K, bp.PATH_MIXED, seed=17, hub_min=hub_min) as s:
+        for side in (0, 1):
+            s.set_state(U, V, hyper, it=6)
+            s.sweep(side)
+            got = s.get_state()[side]
+            ref = oracle_sweep(ds, side, U, V, hy, ds.alpha, 17, 6, structure=st)
+            err = rel_err(got, ref).max()
+            assert err <= TAU_BF16, f"side {side}: {err:.3g}"
+            assert err <= 1e-3, f"side {side}: {err:.3g}"
 
 
 def test_paths_agree_bitwise(gpu_lib):
