@@ -127,23 +127,21 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Gathers neighbours [e, e + cnt) (cnt <= 32) into stage buffer `buf`:
-// warp w fills neighbour chunk w (8 neighbours); lane c owns features
-// 4c .. 4c + 3.  Unused neighbours and features K+1.. are zero.
-__device__ __forceinline__ void tc_gather(const SweepArgs& a, uint8_t* buf, int64_t e, int cnt) {
+// Stage layout: warp w owns neighbour chunk w (8 neighbours) of a 32-neighbour
+// stage; lane c owns features 4c .. 4c + 3 (feature K is the rating).
+// tc_load fetches a lane's 4 x 8 values of neighbours [e, e + cnt) into
+// registers (0 for unused neighbours and features past K); tc_store splits
+// them into bf16 hi/lo and writes them transposed into a stage buffer.
+__device__ __forceinline__ void tc_load(const SweepArgs& a, int64_t e, int cnt, float (&x)[4][8]) {
   const int K = a.K;
-  const int KA = K + 1;
   const int kc = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int groups = (KA + 3) >> 2;
-  if (lane >= groups) return;
   const int f0 = 4 * lane;
   const bool vec = ((K & 3) == 0) && (f0 + 3 < K);
-  float x[4][8];
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     const int k = kc * 8 + n;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    if (k < cnt) {
+    if (k < cnt && f0 <= K) {
       const int64_t j = a.idx[e + k];
       const float* row = a.Vo + j * K;
       if (vec) {
@@ -159,6 +157,12 @@ __device__ __forceinline__ void tc_gather(const SweepArgs& a, uint8_t* buf, int6
     }
     x[0][n] = v0; x[1][n] = v1; x[2][n] = v2; x[3][n] = v3;
   }
+}
+
+__device__ __forceinline__ void tc_store(int K, uint8_t* buf, const float (&x)[4][8]) {
+  const int kc = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f0 = 4 * lane;
+  if (f0 > K) return;  // feature rows past K stay zero
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int m = f0 + i;
@@ -183,6 +187,10 @@ __device__ __forceinline__ int tc_gram(const SweepArgs& a, const TcSmem& s, uint
   const uint32_t idesc = idesc_bf16_f32(kTcM, N);
   const uint32_t base = smem_u32(s.region);
   int issued = 0;
+  // the neighbour values of stage st + 1 are fetched into registers while
+  // stage st is split, stored and issued
+  float xc[4][8], xn[4][8];
+  if (nst > 0) tc_load(a, e0, (int)(n < kTcStage ? n : kTcStage), xc);
   for (int st = 0; st < nst; ++st) {
     const int b = st & 1;
     // one thread sleeps on the barrier; the others wait at the CTA barrier
@@ -193,7 +201,15 @@ __device__ __forceinline__ int tc_gram(const SweepArgs& a, const TcSmem& s, uint
     if (s.flags[1]) break;
     const int64_t e = e0 + (int64_t)st * kTcStage;
     const int cnt = (int)(e1 - e < kTcStage ? e1 - e : kTcStage);
-    tc_gather(a, s.region + b * kTcStageBytes, e, cnt);
+    if (st + 1 < nst) {
+      const int64_t en = e + kTcStage;
+      tc_load(a, en, (int)(e1 - en < kTcStage ? e1 - en : kTcStage), xn);
+    }
+    tc_store(a.K, s.region + b * kTcStageBytes, xc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xc[i][q] = xn[i][q];
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -310,8 +326,8 @@ __device__ __forceinline__ bool tc_cholesky(const TileGeom& G, const TcSmem& s, 
           piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
         }
         piv = live ? piv : 1.0f;
-        const float d = sqrtf(piv);
-        const float rd = 1.0f / d;
+        const float rd = rsqrtf(piv);
+        const float d = piv * rd;
         if (live && m == c0 + j) {
           v[j] = d;
           s.rinv[c0 + j] = rd;
@@ -387,6 +403,37 @@ __device__ __forceinline__ bool tc_cholesky(const TileGeom& G, const TcSmem& s, 
   return s.flags[0] == 0;
 }
 
+// u = L^-T (y + z) by the whole CTA, 16-row blocks from the bottom.  Thread
+// i keeps w_i (initially y_i + z_i, y the bordered row of the factor).  The
+// warp holding a block back-substitutes it with shuffles (x_k = w_k / L_kk,
+// then w_i -= L[k][i] x_k for the block's rows i < k) and publishes x; every
+// thread above the block then subtracts the block's contribution.
+__device__ __forceinline__ void tc_backward_solve(const float* Lr, int LDS, int K,
+                                                  const float* rinv, const float* zv, float* xs,
+                                                  float* __restrict__ xout) {
+  const int i = threadIdx.x, warp = i >> 5;
+  float w = i < K ? Lr[K * LDS + i] + zv[i] : 0.f;
+  for (int b = (K + 15) / 16 - 1; b >= 0; --b) {
+    const int r0 = 16 * b;
+    const int r1 = K < r0 + 16 ? K : r0 + 16;
+    if (warp == (r0 >> 5)) {
+      for (int k = r1 - 1; k >= r0; --k) {
+        const float xk = __shfl_sync(0xffffffffu, w, k & 31) * rinv[k];
+        if (i == k) w = xk;
+        else if (i >= r0 && i < k) w = fmaf(-Lr[k * LDS + i], xk, w);
+      }
+      if (i >= r0 && i < r1) xs[i] = w;
+    }
+    __syncthreads();
+    if (i < r0) {
+      float t = w;
+      for (int k = r0; k < r1; ++k) t = fmaf(-Lr[k * LDS + i], xs[k], t);
+      w = t;
+    }
+  }
+  if (i < K) xout[i] = w;
+}
+
 }  // namespace
 
 // One CTA (128 threads) per row of the row list; Gram and Cholesky on
@@ -423,7 +470,7 @@ __global__ void __launch_bounds__(kTcThreads) row_tc(const SweepArgs a, int* sta
     if (tid == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
     return;
   }
-  if (tid < 32) backward_solve(s.Lr, G.LDS, a.K, s.rinv, s.zv, a.X + (int64_t)row * a.K);
+  tc_backward_solve(s.Lr, G.LDS, a.K, s.rinv, s.zv, s.l11, a.X + (int64_t)row * a.K);
 }
 
 // Partial Gram of one piece of a split row on tensor cores, written as the

@@ -222,8 +222,8 @@ __device__ bool chol_solve_write(float (&acc)[TM][TM], bool active, int ty, int 
             *fail_sh = 1;
             piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
           }
-          const float d = sqrtf(piv);
-          const float rd = 1.0f / d;
+          const float rd = rsqrtf(piv);
+          const float d = piv * rd;
           acc[j][j] = d;
           cs.rinv[c0 + j] = rd;
 #pragma unroll
