@@ -195,6 +195,26 @@ BPMF_API int bpmf_set_timing(bpmf_t *h, int enable);
  * stream.  Errors: EINVAL, ESTATE (timing off), ECUDA. */
 BPMF_API int bpmf_get_timing(bpmf_t *h, double *ms, int64_t *phase_count, int64_t *kernels);
 
+/* Row mean xbar (K doubles) and centred scatter S = sum (x - xbar)(x - xbar)^T
+ * (K*K doubles, row-major) of the R x K float32 factor matrix X, the same
+ * statistics bpmf_sample_hyper reduces, computed without allocating any
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory when they call (a fixed memory pool or
+ * arena they do not own, or a host that forbids cudaMalloc and its implied
+ * synchronisation after start-up).  X, xbar and S are device pointers;
+ * the work is queued on `stream` (a cudaStream_t) and the call returns
+ * without waiting for it.
+ * Scratch: one 2 MiB array compiled into the library, held by every GPU that
+ * loads it until the process exits.  The first call on each device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  All calls share the array,
+ * so calls whose work overlaps on the GPU race; nothing needs clearing between
+ * calls.  The call never calls cudaMalloc, cudaFree or any allocating routine.
+ * Limits: 1 <= K <= 128 and 1 <= R < 2^31; anything else returns EINVAL.
+ * Errors: EINVAL, ECUDA. */
+BPMF_API int bpmf_hyper_stats_noalloc(const float *X, int64_t R, int32_t K, double *xbar,
+                                      double *S, void *stream);
+
 /* Frees the handle and all its device memory.  NULL is ignored. */
 BPMF_API void bpmf_destroy(bpmf_t *h);
 

@@ -20,6 +20,7 @@ __all__ = [
     "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict", "bpmf_test_rmse",
     "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
     "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
+    "bpmf_hyper_stats_noalloc",
     "Sampler", "TIMERS",
     "USERS", "MOVIES", "PATH_PLAIN", "PATH_BINNED", "PATH_MIXED", "DEVPTR",
 ]
@@ -34,6 +35,7 @@ SYMBOLS = [
     "bpmf_step", "bpmf_predict", "bpmf_test_rmse", "bpmf_get_state", "bpmf_set_state",
     "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
     "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
+    "bpmf_hyper_stats_noalloc",
 ]
 TIMERS = ["hyper_reduce", "hyper_draw", "rows_users", "rows_movies", "fp64_redo", "predict"]
 
@@ -92,6 +94,7 @@ def lib():
         L.bpmf_get_sweep_info.argtypes = [P, C.c_int, P, P]
         L.bpmf_set_timing.argtypes = [P, C.c_int]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
+        L.bpmf_hyper_stats_noalloc.argtypes = [P, i64, i32, P, P, P]
         L.bpmf_destroy.argtypes = [P]
         L.bpmf_destroy.restype = None
         L.bpmf_strerror.argtypes = [C.c_int]
@@ -282,6 +285,19 @@ def bpmf_get_timing(h):
     _check(lib().bpmf_get_timing(h, ms.ctypes.data, cnt.ctypes.data, C.byref(k)),
            "bpmf_get_timing")
     return dict(zip(TIMERS, ms.tolist())), dict(zip(TIMERS, cnt.tolist())), k.value
+
+
+def bpmf_hyper_stats_noalloc(X, R, K, xbar, S, stream=None):
+    """Row mean and centred scatter of the device factor matrix X (R x K float32)
+    into the device tensors xbar (K float64) and S (K*K float64), with no
+    allocation (scratch compiled into the library; see include/bpmf.h)."""
+    px, kx, dx = _ptr(X, np.float32)
+    pm, km, dm = _ptr(xbar, np.float64)
+    ps, ks, ds_ = _ptr(S, np.float64)
+    if not (dx and dm and ds_):
+        raise TypeError("bpmf_hyper_stats_noalloc takes device tensors only")
+    _check(lib().bpmf_hyper_stats_noalloc(px, int(R), int(K), pm, ps, _stream_ptr(stream)),
+           "bpmf_hyper_stats_noalloc")
 
 
 def bpmf_destroy(h):

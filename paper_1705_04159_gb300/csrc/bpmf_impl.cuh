@@ -198,6 +198,8 @@ int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch
                            cudaStream_t st);
 int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, cudaStream_t st);
 int launch_hyper_to_f32(Handle* h, int s);
+int launch_stats_into(const float* X, int64_t R, int K, double* part, int blocks, double* xbar,
+                      double* S, float* xbarf, cudaStream_t st);
 
 // rows.cu
 int launch_sweep(Handle* h, int s);

@@ -436,6 +436,23 @@ int launch_hyper(Handle* h, int s) {
   return BPMF_OK;
 }
 
+// The row mean and centred scatter of X (R x K) into xbar and S, with the
+// per-block partials in `part` (blocks * K * K doubles) and the FP32 mean in
+// `xbarf` (K floats); both are caller-provided scratch.
+int launch_stats_into(const float* X, int64_t R, int K, double* part, int blocks, double* xbar,
+                      double* S, float* xbarf, cudaStream_t st) {
+  colsum_partial<<<blocks, kRedThreads, 0, st>>>(X, R, K, part);
+  colsum_final<<<1, kMaxK, 0, st>>>(part, blocks, K, R, xbar, xbarf);
+  if (K <= 16) launch_scatter<1>(X, R, K, xbarf, part, blocks, st);
+  else if (K <= 32) launch_scatter<2>(X, R, K, xbarf, part, blocks, st);
+  else if (K <= 64) launch_scatter<4>(X, R, K, xbarf, part, blocks, st);
+  else if (K <= 112) launch_scatter<7>(X, R, K, xbarf, part, blocks, st);
+  else launch_scatter<8>(X, R, K, xbarf, part, blocks, st);
+  scatter_final<<<(K * K + 255) / 256, 256, 0, st>>>(part, blocks, K, S);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  return BPMF_OK;
+}
+
 int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch, int* status,
                            cudaStream_t st) {
   spd_inverse_kernel<<<1, 512, 0, st>>>(A, Ainv, K, scratch, status);

@@ -1,0 +1,55 @@
+"""The allocation-free entry point bpmf_hyper_stats_noalloc against the
+library's own hyperparameter statistics.
+
+Callers that cannot allocate device memory at call time (a fixed pool or an
+arena they do not own, or a host that forbids cudaMalloc after start-up) use
+bpmf_hyper_stats_noalloc, whose scratch is a fixed array compiled into the
+library.  Its row mean and centred scatter must equal, within the tolerance of
+the other statistics tests, what bpmf_sample_hyper computes for the same
+factors (read back with bpmf_get_hyper_stats), on two calls in a row that
+reuse the shared scratch.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _reference_stats(bp, ds, K, U, V, hyper):
+    with bp.Sampler(ds.M, ds.N, ds.train_row, ds.train_col, ds.train_val, K=K, alpha=ds.alpha,
+                    path=bp.PATH_PLAIN) as s:
+        s.set_state(U, V, hyper, it=1)
+        s.sample_hyper(0)
+        return s.hyper_stats(0)
+
+
+def test_noalloc_stats_match_existing_entry_point_twice(gpu_lib):
+    import torch
+    from parity_util import random_state
+    bp = gpu_lib
+    cases = [(synth.uniform(3000, 200, 20000, 100, seed=31), 100),
+             (synth.uniform(20000, 300, 40000, 32, seed=32), 32)]
+    for ds, K in cases:  # two calls in a row, the second reusing the scratch
+        U, V, hy, hyper = random_state(ds, K)
+        ref_xbar, ref_S = _reference_stats(bp, ds, K, U, V, hyper)
+        X = torch.from_numpy(U).cuda()
+        xbar = torch.full((K,), float("nan"), dtype=torch.float64, device="cuda")
+        S = torch.full((K * K,), float("nan"), dtype=torch.float64, device="cuda")
+        bp.bpmf_hyper_stats_noalloc(X, ds.M, K, xbar, S)
+        torch.cuda.synchronize()
+        got_xbar = xbar.cpu().numpy()
+        got_S = S.cpu().numpy().reshape(K, K)
+        assert np.max(np.abs(got_xbar - ref_xbar)) <= 1e-6 * (np.abs(ref_xbar).max() + U.std())
+        assert np.linalg.norm(got_S - ref_S) <= 1e-5 * np.linalg.norm(ref_S)
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits(gpu_lib):
+    import torch
+    bp = gpu_lib
+    X = torch.zeros((4, 129), dtype=torch.float32, device="cuda")
+    out = torch.zeros(129 * 129, dtype=torch.float64, device="cuda")
+    with pytest.raises(bp.BpmfError) as e:
+        bp.bpmf_hyper_stats_noalloc(X, 4, 129, out, out)
+    assert e.value.code == bp.EINVAL
