@@ -176,6 +176,14 @@ __device__ __forceinline__ double normal_at_f64(uint2 key, uint32_t c0, uint32_t
   return (n & 1u) ? z1 : z0;
 }
 
+// normal number n of the counter base (c0, c1, ., c3) in FP32
+__device__ __forceinline__ float normal_at_f32(uint2 key, uint32_t c0, uint32_t c1, uint32_t c3,
+                                               uint32_t n) {
+  const float4 z = normal4_f32(philox(make_uint4(c0, c1, n >> 2, c3), key));
+  const uint32_t w = n & 3u;
+  return w == 0u ? z.x : (w == 1u ? z.y : (w == 2u ? z.z : z.w));
+}
+
 __host__ __device__ __forceinline__ uint32_t stream_word(uint32_t stream, int side) {
   return (stream << 8) | (uint32_t)side;
 }

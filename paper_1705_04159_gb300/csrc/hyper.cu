@@ -14,7 +14,7 @@
 // Device work: (1) column sums of the factor rows with FP32 partials per block
 // combined in FP64; (2) the centred scatter, a K x K Gram over all rows with
 // FP32 register tiles per block, combined in FP64 in a fixed block order;
-// (3) one CTA in FP64 for the posterior, the three Cholesky factorisations, the
+// (3) one CTA in FP64 for the posterior, one Cholesky factorisation, one
 // triangular inverse and the draws (O(K^3), independent of the row count).
 #include <cuda_runtime.h>
 
@@ -202,17 +202,21 @@ __device__ void cta_ata(const double* A, double* C, int K) {
   __syncthreads();
 }
 
-// Bartlett factor of Wishart(W, nu) with W = C C^T (C lower, given):
-// B = C A, then Lambda = B B^T.  Gamma draws by Marsaglia-Tsang with the
-// attempt number as the counter's third word; the cap flags kStatusRng.
-__device__ void cta_bartlett(const double* C, double* A, double* B, double* Lam, int K, double nu,
-                             uint2 key, uint32_t t, int side, int* status) {
+// Bartlett's lower-triangular A for Wishart(., nu): A_kl ~ N(0, 1) for
+// k > l (normal number k (k - 1) / 2 + l of counter base (0, t, ., WISHART),
+// Box-Muller in FP32 like the row normals: these decide nothing discrete)
+// and A_kk = sqrt(chi^2(nu - k)), chi^2(m) = 2 Gamma(m / 2) by Marsaglia-Tsang
+// in FP64 with the attempt number as the counter's third word (counter (k, t,
+// a, GAMMA)); the acceptance test decides which attempt is kept, so it runs
+// in FP64 like the reference.  The attempt cap flags kStatusRng.
+__device__ void cta_bartlett_A(double* A, int K, double nu, uint2 key, uint32_t t, int side,
+                               int* status) {
   const uint32_t sw_w = stream_word(kStreamWishart, side);
   const uint32_t sw_g = stream_word(kStreamGamma, side);
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int k = e / K, l = e % K;
     double v = 0.0;
-    if (l < k) v = normal_at_f64(key, 0u, t, sw_w, (uint32_t)(k * (k - 1) / 2 + l));
+    if (l < k) v = (double)normal_at_f32(key, 0u, t, sw_w, (uint32_t)(k * (k - 1) / 2 + l));
     A[e] = v;
   }
   __syncthreads();
@@ -240,22 +244,6 @@ __device__ void cta_bartlett(const double* C, double* A, double* B, double* Lam,
       g = s;
     }
     A[k * K + k] = sqrt(2.0 * g);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int i = e / K, j = e % K;
-    double v = 0.0;
-    if (j <= i)
-      for (int m = j; m <= i; ++m) v += C[i * K + m] * A[m * K + j];
-    B[e] = v;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int i = e / K, j = e % K;
-    const int top = min(i, j);
-    double v = 0.0;
-    for (int m = 0; m <= top; ++m) v += B[i * K + m] * B[j * K + m];
-    Lam[e] = v;
   }
   __syncthreads();
 }
@@ -294,54 +282,70 @@ struct HyperArgs {
   int* status;
 };
 
+// The posterior draw.  Two exact identities keep the FP64 work to about
+// K^3 / 6 multiply-adds per step:
+//  * C = chol(W*) without forming W* = (W*^-1)^-1: with J the reversal
+//    permutation and L_M = chol(J W*^-1 J), W*^-1 = (J L_M J)(J L_M J)^T with
+//    J L_M J upper triangular, so W* = (J L_M^-T J)(J L_M^-T J)^T and
+//    C = J L_M^-T J, i.e. C[i][j] = T[K-1-j][K-1-i] with T = L_M^-1
+//    (lower triangular with a positive diagonal, hence the Cholesky factor);
+//  * chol(beta* Lambda) = sqrt(beta*) B for B = C A (lower triangular with a
+//    positive diagonal and Lambda = B B^T), so mu = mu* + B^-T z / sqrt(beta*).
 __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
   __shared__ int bad;
   const int K = a.K, KK = K * K;
-  double* Wi = a.scr;          // W*^-1, then its Cholesky factor P
-  double* Pinv = Wi + KK;      // P^-1
-  double* Ws = Pinv + KK;      // W*, then C = chol(W*)
-  double* A = Ws + KK;         // Bartlett A
+  double* Mx = a.scr;          // J W*^-1 J, then its Cholesky factor L_M
+  double* T = Mx + KK;         // L_M^-1
+  double* A = T + KK;          // Bartlett A
   double* B = A + KK;          // C A
-  double* Lm = B + KK;         // chol(beta* Lambda)
-  double* mus = Lm + KK;       // mu*
+  double* mus = B + KK;        // mu*
   double* x = mus + K;         // solve workspace
   const double n = (double)a.n;
   const double w = a.beta0 * n / (a.beta0 + n);
   for (int e = threadIdx.x; e < KK; e += blockDim.x) {
-    const int i = e / K, j = e % K;
-    Wi[e] = a.W0inv[e] + a.S[e] + w * (a.mu0[i] - a.xbar[i]) * (a.mu0[j] - a.xbar[j]);
+    const int i = K - 1 - e / K, j = K - 1 - e % K;
+    Mx[e] = a.W0inv[i * K + j] + a.S[i * K + j] + w * (a.mu0[i] - a.xbar[i]) * (a.mu0[j] - a.xbar[j]);
   }
   for (int k = threadIdx.x; k < K; k += blockDim.x)
     mus[k] = (a.beta0 * a.mu0[k] + n * a.xbar[k]) / (a.beta0 + n);
   __syncthreads();
   const double beta_s = a.beta0 + n, nu_s = a.nu0 + n;
-  if (!cta_cholesky(Wi, K, &bad)) {
+  if (!cta_cholesky(Mx, K, &bad)) {
     if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
     return;
   }
-  cta_tri_inverse(Wi, Pinv, K);
-  cta_ata(Pinv, Ws, K);  // W* = P^-T P^-1
-  if (!cta_cholesky(Ws, K, &bad)) {
-    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
-    return;
-  }
+  cta_tri_inverse(Mx, T, K);
   const uint2 key = seed_key(a.seed);
-  cta_bartlett(Ws, A, B, a.lam, K, nu_s, key, a.t, a.side, a.status);
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) Lm[e] = beta_s * a.lam[e];
-  __syncthreads();
-  if (!cta_cholesky(Lm, K, &bad)) {
-    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
-    return;
+  cta_bartlett_A(A, K, nu_s, key, a.t, a.side, a.status);
+  // B = C A on the lower triangle, C[i][m] = T[K-1-m][K-1-i]
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    double v = 0.0;
+    if (j <= i)
+      for (int m = j; m <= i; ++m) v += T[(K - 1 - m) * K + (K - 1 - i)] * A[m * K + j];
+    B[e] = v;
   }
-  // mu = mu* + Lm^-T z, back substitution by one thread (K <= 128 steps)
+  __syncthreads();
+  // Lambda = B B^T (lower triangle, mirrored)
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    if (j > i) continue;
+    double v = 0.0;
+    for (int m = 0; m <= j; ++m) v += B[i * K + m] * B[j * K + m];
+    a.lam[i * K + j] = v;
+    a.lam[j * K + i] = v;
+  }
+  __syncthreads();
+  // mu = mu* + B^-T z / sqrt(beta*), back substitution by one thread
   if (threadIdx.x == 0) {
     const uint32_t sw = stream_word(kStreamHyperMu, a.side);
     for (int i = K - 1; i >= 0; --i) {
-      double v = normal_at_f64(key, 0u, a.t, sw, (uint32_t)i);
-      for (int k = i + 1; k < K; ++k) v -= Lm[k * K + i] * x[k];
-      x[i] = v / Lm[i * K + i];
+      double v = (double)normal_at_f32(key, 0u, a.t, sw, (uint32_t)i);
+      for (int k = i + 1; k < K; ++k) v -= B[k * K + i] * x[k];
+      x[i] = v / B[i * K + i];
     }
-    for (int i = 0; i < K; ++i) a.mu[i] = mus[i] + x[i];
+    const double rb = 1.0 / sqrt(beta_s);
+    for (int i = 0; i < K; ++i) a.mu[i] = mus[i] + x[i] * rb;
   }
   __syncthreads();
   write_bordered(a.lam, a.mu, K, a.lamaug);

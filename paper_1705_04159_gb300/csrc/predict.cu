@@ -1,11 +1,12 @@
 // predict.cu -- test predictions (Algorithm 1, "for all test points:
 // predict rating and compute RMSE").
 //
-// r_hat = u_row . v_col + mean.  One warp per pair reads both factor rows
-// coalesced and reduces with shuffles.  The registered test set is sorted by
-// user at registration so consecutive warps reuse the same user row.  Squared
-// errors of the latest sample and of the running mean of predictions are
-// reduced per block in FP64 and combined in block order (deterministic).
+// r_hat = u_row . v_col + mean.  One thread per pair reads both factor rows
+// with 16-byte loads (many pairs in flight per SM).  The registered test set
+// is sorted by user at registration, so neighbouring threads share the user
+// row through L1.  Squared errors of the latest sample and of the running
+// mean of predictions are reduced per block in FP64 and combined in block
+// order (deterministic).
 #include <cuda_runtime.h>
 
 #include "bpmf_impl.cuh"
@@ -16,23 +17,32 @@ namespace {
 constexpr int kPredThreads = 256;
 constexpr int kPredWarps = kPredThreads / 32;
 
-__device__ __forceinline__ float warp_dot(const float* __restrict__ u, const float* __restrict__ v,
-                                          int K, int lane) {
+__device__ __forceinline__ float row_dot(const float* __restrict__ u, const float* __restrict__ v,
+                                         int K) {
   float s = 0.f;
-  for (int k = lane; k < K; k += 32) s = fmaf(__ldg(u + k), __ldg(v + k), s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((K & 3) == 0) {
+    const float4* a = reinterpret_cast<const float4*>(u);
+    const float4* b = reinterpret_cast<const float4*>(v);
+    for (int q = 0; q < (K >> 2); ++q) {
+      const float4 x = __ldg(a + q), y = __ldg(b + q);
+      s = fmaf(x.x, y.x, s);
+      s = fmaf(x.y, y.y, s);
+      s = fmaf(x.z, y.z, s);
+      s = fmaf(x.w, y.w, s);
+    }
+  } else {
+    for (int k = 0; k < K; ++k) s = fmaf(__ldg(u + k), __ldg(v + k), s);
+  }
   return s;
 }
 
 __global__ void predict_pairs(const float* __restrict__ U, const float* __restrict__ V, int K,
                               double mean, const int32_t* __restrict__ row,
                               const int32_t* __restrict__ col, int64_t n, float* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (int64_t)blockIdx.x * kPredWarps + (threadIdx.x >> 5);
-  for (int64_t p = w0; p < n; p += (int64_t)gridDim.x * kPredWarps) {
-    const float s = warp_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K, lane);
-    if (lane == 0) out[p] = (float)((double)s + mean);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float s = row_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K);
+    out[p] = (float)((double)s + mean);
   }
 }
 
@@ -44,21 +54,24 @@ __global__ void test_errors(const float* __restrict__ U, const float* __restrict
   __shared__ double es[kPredWarps], em[kPredWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double e1 = 0.0, e2 = 0.0;
-  const int64_t w0 = (int64_t)blockIdx.x * kPredWarps + warp;
-  for (int64_t p = w0; p < n; p += (int64_t)gridDim.x * kPredWarps) {
-    const float s = warp_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K, lane);
-    if (lane == 0) {
-      const double pred = (double)s + mean;
-      const double d = pred - (double)truth[p];
-      e1 += d * d;
-      double acc = sum[p];
-      if (accumulate) {
-        acc += pred;
-        sum[p] = acc;
-      }
-      const double dm = acc * inv_avg - (double)truth[p];
-      e2 += dm * dm;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float s = row_dot(U + (int64_t)row[p] * K, V + (int64_t)col[p] * K, K);
+    const double pred = (double)s + mean;
+    const double d = pred - (double)truth[p];
+    e1 += d * d;
+    double acc = sum[p];
+    if (accumulate) {
+      acc += pred;
+      sum[p] = acc;
     }
+    const double dm = acc * inv_avg - (double)truth[p];
+    e2 += dm * dm;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e1 += __shfl_down_sync(0xffffffffu, e1, o);
+    e2 += __shfl_down_sync(0xffffffffu, e2, o);
   }
   if (lane == 0) {
     es[warp] = e1;
@@ -90,7 +103,7 @@ __global__ void test_final(const double* __restrict__ part, int blocks, int64_t 
 }
 
 int pred_blocks(Handle* h, int64_t n) {
-  int64_t b = (n + kPredWarps - 1) / kPredWarps;
+  int64_t b = (n + kPredThreads - 1) / kPredThreads;
   const int64_t cap = 8LL * h->num_sms;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
