@@ -133,9 +133,20 @@ BPMF_API int bpmf_sweep(bpmf_t *h, int side);
 
 /* One Gibbs iteration (Algorithm 1's loop body): for each side in `order`,
  * bpmf_sample_hyper then bpmf_sweep; then the test predictions (if a test
- * set is registered); then the iteration counter advances.  Errors: as the
- * calls it makes. */
+ * set is registered); then the iteration counter advances.  Unless graphs
+ * are switched off (bpmf_set_graph), the first call records the iteration's
+ * launches as a CUDA graph and every call replays it on the handle's stream;
+ * the iteration counter and the running-mean count live in device memory, so
+ * the replays draw exactly what the direct launches would.  A new test set or
+ * a change of the timing switch makes the next call record it again.
+ * Synchronises the stream.  Errors: as the calls it makes. */
 BPMF_API int bpmf_step(bpmf_t *h);
+
+/* Switches the CUDA graph of bpmf_step on (enable != 0, the default) or off
+ * (direct launches).  The paper has no counterpart: this is a launch
+ * mechanism only, and results are bitwise the same either way.
+ * Errors: EINVAL. */
+BPMF_API int bpmf_set_graph(bpmf_t *h, int enable);
 
 /* Predictions r = u_row . v_col + mean for n pairs from the current sample
  * into out[n] (float32).  Errors: EINVAL, ECUDA. */

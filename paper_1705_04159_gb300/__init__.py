@@ -20,7 +20,7 @@ __all__ = [
     "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict", "bpmf_test_rmse",
     "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
     "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
-    "bpmf_hyper_stats_noalloc",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph",
     "Sampler", "TIMERS",
     "USERS", "MOVIES", "PATH_PLAIN", "PATH_BINNED", "PATH_MIXED", "DEVPTR",
 ]
@@ -35,7 +35,7 @@ SYMBOLS = [
     "bpmf_step", "bpmf_predict", "bpmf_test_rmse", "bpmf_get_state", "bpmf_set_state",
     "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
     "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
-    "bpmf_hyper_stats_noalloc",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph",
 ]
 TIMERS = ["hyper_reduce", "hyper_draw", "rows_users", "rows_movies", "fp64_redo", "predict"]
 
@@ -93,6 +93,7 @@ def lib():
         L.bpmf_get_hyper_stats.argtypes = [P, C.c_int, P, P]
         L.bpmf_get_sweep_info.argtypes = [P, C.c_int, P, P]
         L.bpmf_set_timing.argtypes = [P, C.c_int]
+        L.bpmf_set_graph.argtypes = [P, C.c_int]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
         L.bpmf_hyper_stats_noalloc.argtypes = [P, i64, i32, P, P, P]
         L.bpmf_destroy.argtypes = [P]
@@ -277,6 +278,10 @@ def bpmf_set_timing(h, enable=True):
     _check(lib().bpmf_set_timing(h, 1 if enable else 0), "bpmf_set_timing")
 
 
+def bpmf_set_graph(h, enable=True):
+    _check(lib().bpmf_set_graph(h, 1 if enable else 0), "bpmf_set_graph")
+
+
 def bpmf_get_timing(h):
     """({timer: ms}, {timer: phases}, kernels launched) since timing was enabled."""
     ms = np.zeros(len(TIMERS))
@@ -383,6 +388,9 @@ class Sampler:
 
     def timing(self):
         return bpmf_get_timing(self.h)
+
+    def set_graph(self, enable=True):
+        bpmf_set_graph(self.h, enable)
 
     def hyper(self):
         """(Lambda_U, mu_U, Lambda_V, mu_V) from the packed state."""

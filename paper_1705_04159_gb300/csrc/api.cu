@@ -48,7 +48,9 @@ void dfree(void* p) {
 
 void free_handle(Handle* h) {
   if (!h) return;
+  drop_graph(h);
   release_timers(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhl);
@@ -57,7 +59,7 @@ void free_handle(Handle* h) {
   }
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
   dfree(h->flag_rows); dfree(h->flag_count); dfree(h->trow); dfree(h->tcol); dfree(h->tval);
-  dfree(h->tsum); dfree(h->terr); dfree(h->hub_part);
+  dfree(h->tsum); dfree(h->terr); dfree(h->hub_part); dfree(h->d_iter); dfree(h->d_navg);
   delete h;
 }
 
@@ -113,6 +115,84 @@ int read_fp64_rows(Handle* h, int s) {
                                   h->stream));
   BPMF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   h->side[s].fp64_rows = n;
+  return BPMF_OK;
+}
+
+// One Gibbs iteration (Algorithm 1): per side in the configured order the
+// hyperparameter draw then the row draws, then the test predictions, then
+// the iteration word advances.  Everything that changes from one iteration
+// to the next lives in device memory, so the same launches serve every
+// iteration.
+int step_body(Handle* h) {
+  const int first = h->cfg.order == 0 ? BPMF_USERS : BPMF_MOVIES;
+  for (int q = 0; q < 2; ++q) {
+    const int s = q == 0 ? first : 1 - first;
+    BPMF_TRY(launch_hyper(h, s));
+    BPMF_TRY(sweep_one(h, s));
+  }
+  BPMF_TRY(launch_test_step(h));
+  return launch_advance_iter(h);
+}
+
+// Records step_body into an executable graph.  The capture runs on a private
+// stream (the legacy default stream cannot be captured); replays go to the
+// handle's stream.  Phase timers become event-record nodes whose pairs are
+// read after every replay.
+int capture_step(Handle* h) {
+  if (!h->cap_stream)
+    BPMF_CUDA_CHECK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  const int64_t k0 = h->kernels;
+  const size_t p0 = h->pending.size();
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  BPMF_CUDA_CHECK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+  h->capturing = true;
+  int rc = step_body(h);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+  h->capturing = false;
+  h->stream = user;
+  const int64_t per = h->kernels - k0;
+  h->kernels = k0;
+  std::vector<Handle::Pending> timers(h->pending.begin() + (std::ptrdiff_t)p0, h->pending.end());
+  h->pending.resize(p0);
+  if (rc == BPMF_OK && ec != cudaSuccess) {
+    set_error("bpmf_step: graph capture: %s", cudaGetErrorString(ec));
+    rc = BPMF_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (rc == BPMF_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    if (ei != cudaSuccess) {
+      set_error("bpmf_step: graph instantiate: %s", cudaGetErrorString(ei));
+      rc = BPMF_ECUDA;
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  if (rc != BPMF_OK) {
+    cudaGetLastError();
+    for (auto& p : timers) {
+      h->event_pool.push_back(p.a);
+      h->event_pool.push_back(p.b);
+    }
+    return rc;
+  }
+  h->graph = ex;
+  h->graph_timing = h->timing;
+  h->graph_kernels = per;
+  h->graph_timers = timers;
+  return BPMF_OK;
+}
+
+// Adds the phase times of the last replay (the stream is idle).
+int resolve_graph_timers(Handle* h) {
+  for (auto& p : h->graph_timers) {
+    float ms = 0.f;
+    BPMF_CUDA_CHECK(cudaEventElapsedTime(&ms, p.a, p.b));
+    h->t_ms[p.id] += ms;
+    h->t_cnt[p.id] += 1;
+  }
   return BPMF_OK;
 }
 
@@ -222,7 +302,11 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     if ((rc = dalloc(&h->flag_count, 1))) break;
     if ((rc = dalloc(&h->flag_rows, std::max(M, N)))) break;
     if ((rc = dalloc(&h->terr, 2))) break;
-    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+    if ((rc = dalloc(&h->d_iter, 1))) break;
+    if ((rc = dalloc(&h->d_navg, 1))) break;
+    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->d_iter, 0, sizeof(uint32_t), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->d_navg, 0, sizeof(int64_t), h->stream) != cudaSuccess) {
       rc = BPMF_ECUDA;
       break;
     }
@@ -291,6 +375,9 @@ int bpmf_set_test(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col,
   }
   const bool dev = (flags & BPMF_DEVPTR) != 0;
   cudaStream_t st = h->stream;
+  drop_graph(h);  // the captured iteration holds the old test arrays
+  BPMF_CUDA_CHECK(cudaMemsetAsync(h->d_navg, 0, sizeof(int64_t), st));
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
   dfree(h->trow); dfree(h->tcol); dfree(h->tval); dfree(h->tsum);
   h->trow = h->tcol = nullptr;
   h->tval = nullptr;
@@ -357,15 +444,30 @@ int bpmf_sweep(bpmf_t* hh, int side) {
 int bpmf_step(bpmf_t* hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return BPMF_EINVAL;
-  const int first = h->cfg.order == 0 ? BPMF_USERS : BPMF_MOVIES;
-  for (int q = 0; q < 2; ++q) {
-    const int s = q == 0 ? first : 1 - first;
-    BPMF_TRY(launch_hyper(h, s));
-    BPMF_TRY(sweep_one(h, s));
+  if (h->use_graph) {
+    if (h->graph && h->graph_timing != h->timing) drop_graph(h);
+    if (!h->graph) BPMF_TRY(capture_step(h));
+    BPMF_CUDA_CHECK(cudaGraphLaunch(h->graph, h->stream));
+    h->kernels += h->graph_kernels;
+  } else {
+    BPMF_TRY(step_body(h));
   }
-  BPMF_TRY(launch_test_step(h, h->iter >= h->cfg.burnin));
+  if (h->n_test > 0) {
+    if (h->iter >= h->cfg.burnin) h->n_avg += 1;
+    h->have_rmse = true;
+  }
   h->iter += 1;
-  return check_status(h, "bpmf_step");
+  const int rc = check_status(h, "bpmf_step");
+  if (rc == BPMF_OK && h->use_graph && h->timing) BPMF_TRY(resolve_graph_timers(h));
+  return rc;
+}
+
+int bpmf_set_graph(bpmf_t* hh, int enable) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return BPMF_EINVAL;
+  drop_graph(h);
+  h->use_graph = enable != 0;
+  return BPMF_OK;
 }
 
 int bpmf_predict(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col, float* out,
@@ -468,6 +570,9 @@ int bpmf_set_state(bpmf_t* hh, const float* U, const float* V, const double* hyp
     h->side[0].have_hyper = h->side[1].have_hyper = true;
   }
   h->iter = iter;
+  const uint32_t t32 = (uint32_t)iter;
+  BPMF_CUDA_CHECK(cudaMemcpyAsync(h->d_iter, &t32, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                  h->stream));
   BPMF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
   return BPMF_OK;
 }
@@ -538,7 +643,9 @@ static cudaEvent_t take_event(Handle* h) {
 PhaseTimer::PhaseTimer(Handle* h_, int id_) : h(h_), id(id_) {
   if (!h->timing) return;
   a = take_event(h);
-  if (a) cudaEventRecord(a, h->stream);
+  if (!a) return;
+  if (h->capturing) cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(a, h->stream);
 }
 
 PhaseTimer::~PhaseTimer() {
@@ -548,7 +655,8 @@ PhaseTimer::~PhaseTimer() {
     h->event_pool.push_back(a);
     return;
   }
-  cudaEventRecord(b, h->stream);
+  if (h->capturing) cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(b, h->stream);
   h->pending.push_back({a, b, id});
 }
 
@@ -565,6 +673,21 @@ int resolve_timers(Handle* h) {
   }
   h->pending.clear();
   return BPMF_OK;
+}
+
+void drop_graph(Handle* h) {
+  if (h->graph) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  for (auto& p : h->graph_timers) {
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->graph_timers.clear();
+  h->graph_kernels = 0;
 }
 
 void release_timers(Handle* h) {

@@ -88,9 +88,22 @@ struct Handle {
   float* tval = nullptr;
   double* tsum = nullptr;    // running sum of predictions
   double* terr = nullptr;    // [2] sample / mean squared error
-  int64_t n_avg = 0;
+  int64_t n_avg = 0;         // host mirror of *d_navg
   bool have_rmse = false;
-  int64_t iter = 0;
+  int64_t iter = 0;          // host mirror of *d_iter
+  // per-iteration state read by the kernels, so that one captured iteration
+  // replays for every iteration
+  uint32_t* d_iter = nullptr;  // Gibbs iteration (Philox counter word)
+  int64_t* d_navg = nullptr;   // samples in the running mean of predictions
+  // one Gibbs iteration (both hyper draws, both half-sweeps, test step,
+  // iteration advance) as an executable CUDA graph, captured on first use
+  bool use_graph = true;
+  bool capturing = false;
+  cudaStream_t cap_stream = nullptr;  // private stream the capture runs on
+  cudaGraphExec_t graph = nullptr;
+  bool graph_timing = false;          // timing state the graph was captured with
+  int64_t graph_kernels = 0;          // kernels per replay
+
   // hub split partial Grams
   float* hub_part = nullptr;
   int64_t hub_part_len = 0;
@@ -98,6 +111,7 @@ struct Handle {
   bool timing = false;
   struct Pending { cudaEvent_t a, b; int id; };
   std::vector<Pending> pending;
+  std::vector<Pending> graph_timers;  // event nodes of the captured iteration
   std::vector<cudaEvent_t> event_pool;
   double t_ms[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
   int64_t t_cnt[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
@@ -114,6 +128,7 @@ struct PhaseTimer {
 };
 int resolve_timers(Handle* h);
 void release_timers(Handle* h);
+void drop_graph(Handle* h);
 
 // ---------------------------------------------------------------- Philox --
 // Philox4x32-10: ten rounds, each two 32x32 -> 64-bit products by the
@@ -216,7 +231,8 @@ int launch_refresh_shadow(Handle* h, int s);
 
 // predict.cu
 int launch_predict(Handle* h, int64_t n, const int32_t* r, const int32_t* c, float* out);
-int launch_test_step(Handle* h, bool accumulate);
+int launch_test_step(Handle* h);
+int launch_advance_iter(Handle* h);
 
 // api.cu
 void set_error(const char* fmt, ...);

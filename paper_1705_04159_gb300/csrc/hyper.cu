@@ -272,7 +272,7 @@ struct HyperArgs {
   double beta0, nu0;
   const double* W0inv;
   uint64_t seed;
-  uint32_t t;
+  const uint32_t* tp;  // iteration word on the device
   int side;
   int K;
   double* scr;  // 6 K*K + 2 K doubles
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
   }
   cta_tri_inverse(Mx, T, K);
   const uint2 key = seed_key(a.seed);
-  cta_bartlett_A(A, K, nu_s, key, a.t, a.side, a.status);
+  const uint32_t t = *a.tp;
+  cta_bartlett_A(A, K, nu_s, key, t, a.side, a.status);
   // B = C A on the lower triangle, C[i][m] = T[K-1-m][K-1-i]
   for (int e = threadIdx.x; e < KK; e += blockDim.x) {
     const int i = e / K, j = e % K;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
   if (threadIdx.x == 0) {
     const uint32_t sw = stream_word(kStreamHyperMu, a.side);
     for (int i = K - 1; i >= 0; --i) {
-      double v = (double)normal_at_f32(key, 0u, a.t, sw, (uint32_t)i);
+      double v = (double)normal_at_f32(key, 0u, t, sw, (uint32_t)i);
       for (int k = i + 1; k < K; ++k) v -= B[k * K + i] * x[k];
       x[i] = v / B[i * K + i];
     }
@@ -421,7 +422,7 @@ int launch_hyper(Handle* h, int s) {
   a.nu0 = h->cfg.nu0;
   a.W0inv = h->W0inv;
   a.seed = h->cfg.seed;
-  a.t = (uint32_t)h->iter;
+  a.tp = h->d_iter;
   a.side = s;
   a.K = K;
   a.scr = h->wscr;

@@ -49,10 +49,16 @@ __global__ void predict_pairs(const float* __restrict__ U, const float* __restri
 __global__ void test_errors(const float* __restrict__ U, const float* __restrict__ V, int K,
                             double mean, const int32_t* __restrict__ row,
                             const int32_t* __restrict__ col, const float* __restrict__ truth,
-                            int64_t n, double* __restrict__ sum, int accumulate, double inv_avg,
+                            int64_t n, double* __restrict__ sum, const uint32_t* __restrict__ tp,
+                            int64_t burnin, const int64_t* __restrict__ navg,
                             double* __restrict__ part) {
   __shared__ double es[kPredWarps], em[kPredWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // samples after burn-in enter the running mean; the count is read on the
+  // device so that one captured iteration serves every iteration
+  const bool accumulate = (int64_t)*tp >= burnin;
+  const int64_t n_avg = *navg + (accumulate ? 1 : 0);
+  const double inv_avg = n_avg > 0 ? 1.0 / (double)n_avg : 0.0;
   double e1 = 0.0, e2 = 0.0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -90,8 +96,10 @@ __global__ void test_errors(const float* __restrict__ U, const float* __restrict
 }
 
 __global__ void test_final(const double* __restrict__ part, int blocks, int64_t n,
-                           double* __restrict__ out) {
+                           double* __restrict__ out, const uint32_t* __restrict__ tp,
+                           int64_t burnin, int64_t* __restrict__ navg) {
   if (threadIdx.x == 0) {
+    if ((int64_t)*tp >= burnin) *navg += 1;
     double a = 0.0, b = 0.0;
     for (int i = 0; i < blocks; ++i) {
       a += part[2 * i];
@@ -121,19 +129,28 @@ int launch_predict(Handle* h, int64_t n, const int32_t* r, const int32_t* c, flo
   return BPMF_OK;
 }
 
-int launch_test_step(Handle* h, bool accumulate) {
+int launch_test_step(Handle* h) {
   if (h->n_test <= 0) return BPMF_OK;
-  if (accumulate) h->n_avg += 1;
-  const double inv = h->n_avg > 0 ? 1.0 / (double)h->n_avg : 0.0;
   const int blocks = pred_blocks(h, h->n_test);
   PhaseTimer timer(h, BPMF_T_PREDICT);
   h->kernels += 2;
   test_errors<<<blocks, kPredThreads, 0, h->stream>>>(
       h->side[BPMF_USERS].X, h->side[BPMF_MOVIES].X, h->K, h->mean, h->trow, h->tcol, h->tval,
-      h->n_test, h->tsum, accumulate ? 1 : 0, inv, h->red);
-  test_final<<<1, 32, 0, h->stream>>>(h->red, blocks, h->n_test, h->terr);
+      h->n_test, h->tsum, h->d_iter, h->cfg.burnin, h->d_navg, h->red);
+  test_final<<<1, 32, 0, h->stream>>>(h->red, blocks, h->n_test, h->terr, h->d_iter,
+                                      h->cfg.burnin, h->d_navg);
   BPMF_CUDA_CHECK(cudaGetLastError());
-  h->have_rmse = true;
+  return BPMF_OK;
+}
+
+__global__ void advance_iter(uint32_t* __restrict__ tp) {
+  if (threadIdx.x == 0) *tp += 1u;
+}
+
+int launch_advance_iter(Handle* h) {
+  h->kernels += 1;
+  advance_iter<<<1, 32, 0, h->stream>>>(h->d_iter);
+  BPMF_CUDA_CHECK(cudaGetLastError());
   return BPMF_OK;
 }
 

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
   int ty = 0, tx = 0;
   if (active) tri_tile(tid, G.g, ty, tx);
   if (tid == 0) fail_sh = 0;
-  row_normals(s.zv, a.K, row, a.t, a.sw, a.key);
+  row_normals(s.zv, a.K, row, *a.tp, a.sw, a.key);
 
   float acc[TM][TM];
 #pragma unroll
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) row_fp64(const SweepArgs a, const double*
         for (int k = 0; k < i; ++k) t -= A[i * K + k] * y[k];
         y[i] = t / A[i * K + i];
       }
-      for (int i = 0; i < K; ++i) y[i] += normal_at_f64(a.key, (uint32_t)row, a.t, a.sw, (uint32_t)i);
+      for (int i = 0; i < K; ++i) y[i] += normal_at_f64(a.key, (uint32_t)row, *a.tp, a.sw, (uint32_t)i);
       for (int i = K - 1; i >= 0; --i) {
         double t = y[i];
         for (int k = i + 1; k < K; ++k) t -= A[k * K + i] * b[k];
@@ -356,7 +356,7 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.K = h->K;
   a.alpha = (float)h->cfg.alpha;
   a.key = seed_key(h->cfg.seed);
-  a.t = (uint32_t)h->iter;
+  a.tp = h->d_iter;
   a.sw = stream_word(kStreamRow, s);
   a.flag_rows = h->flag_rows;
   a.flag_count = h->flag_count;

@@ -20,7 +20,7 @@ struct SweepArgs {
   int K;
   float alpha;
   uint2 key;            // Philox key
-  uint32_t t;           // iteration
+  const uint32_t* tp;   // iteration word on the device (read by each CTA)
   uint32_t sw;          // stream word (ROW << 8 | side)
   int32_t* flag_rows;   // rows whose FP32 pivot failed
   int32_t* flag_count;

@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(kTcThreads) row_tc(const SweepArgs a, int* sta
   tc_setup(s);
   const uint32_t tmem = *s.taddr;
   const uint32_t trow = tmem + ((uint32_t)(32 * (tid >> 5)) << 16);
-  row_normals(s.zv, a.K, row, a.t, a.sw, a.key);
+  row_normals(s.zv, a.K, row, *a.tp, a.sw, a.key);
 
   const int issued = tc_gram(a, s, tmem, N, a.ptr[row], a.ptr[row + 1]);
   bool ok = s.flags[1] == 0;
