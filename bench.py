@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-jobs", type=int, default=256)
+    p.add_argument("--serving-iters", type=int, default=50)
     p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],
                    help="execution path of the main arm")
     p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
@@ -233,6 +236,44 @@ def device_arm(bp, ds, path, steps, warmup, world, stream):
                 rmse=rmse, info=info)
 
 
+def serving_arm(bp, n_jobs, iterations, seed=0):
+    """The serving stream: independent jobs submitted at their Poisson arrival
+    times to the continuous-batching server; latency = completion - arrival."""
+    import synth
+    import torch
+    specs = synth.serving_stream(n_jobs, 20.0, seed)
+    t0 = time.perf_counter()
+    jobs = [synth.serving_job(sp, "cuda") for sp in specs]
+    gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    with bp.Server() as srv:
+        start = time.perf_counter()
+        ids = []
+        for sp, ds in zip(specs, jobs):
+            delay = start + sp["arrival_s"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(ds.M, ds.N, ds.train_row, ds.train_col, ds.train_val, ds.K,
+                                  iterations, test=(ds.test_row, ds.test_col, ds.test_val),
+                                  alpha=ds.alpha, seed=sp["seed"], path=bp.PATH_MIXED))
+        res = [srv.result(j)[0] for j in ids]
+        st = srv.stats()
+    ok = [r for r in res if r.status == 0]
+    lat = sorted((r.t_end - r.t_submit) * 1e3 for r in ok)
+    q = lambda f: lat[min(len(lat) - 1, int(math.ceil(f * len(lat))) - 1)] if lat else None
+    span = max(r.t_end for r in ok) - min(r.t_submit for r in ok) if ok else float("nan")
+    rows = sum((ds.M + ds.N) * r.iterations for ds, r in zip(jobs, res) if r.status == 0)
+    return {"jobs": n_jobs, "completed": len(ok), "iterations": iterations,
+            "rate_per_s": 20.0, "p50_ms": q(0.50), "p99_ms": q(0.99),
+            "mean_ms": statistics.mean(lat) if lat else None,
+            "rows_per_s": rows / span if ok else None, "makespan_s": span,
+            "peak_resident": st["peak_resident"], "budget_gb": st["budget"] / 1e9,
+            "peak_budgeted_gb": st["peak_bytes"] / 1e9, "generate_s": gen_s,
+            "workload": "256 jobs, Poisson 20/s, rows log-U[1k,200k], cols log-U[1k,50k], "
+                        "ratings log-U[10k,5M], K in {16,32,64}, mixed path"}
+
+
 def e2e_arm(bp, ds, path, steps, stream):
     """A whole job through the C ABI from pinned host buffers: bpmf_init (H2D of
     the ratings, structure build), bpmf_set_test, `steps` iterations, then the
@@ -377,6 +418,10 @@ def main():
                 "flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                 "ms_per_launch": per[dom]}
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_arm(bp, args.serving_jobs, args.serving_iters, seed=args.seed)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, cores, parts = cpu_oracle_rate(ds, K, args.cpu_budget)
@@ -398,6 +443,7 @@ def main():
             "bins": {"users": mixed["info"][0][0].tolist(), "movies": mixed["info"][1][0].tolist(),
                      "fp64_rows": [mixed["info"][0][1], mixed["info"][1][1]]},
             "plain_fp32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:

@@ -54,6 +54,7 @@ extern "C" {
 #define BPMF_ENOTPD (-4)  /* a precision matrix was not positive definite even in FP64 */
 #define BPMF_ERNG (-5)    /* the Gamma sampler exceeded its rejection cap (64) */
 #define BPMF_ESTATE (-6)  /* call out of order (e.g. a sweep before any hyper draw) */
+#define BPMF_EBUSY (-7)   /* the job has not finished yet (bpmf_server_poll) */
 
 /* ---- sides ---- */
 #define BPMF_USERS 0
@@ -85,12 +86,19 @@ typedef struct {
   uint64_t seed;      /* Philox key */
   int32_t order;      /* 0: users then movies in an iteration; 1: movies then users */
   int32_t burnin;     /* iterations before the running mean of predictions starts */
-  int32_t light_max;  /* rows with degree <= light_max take the light kernel; -1: automatic */
+  int32_t light_max;  /* rows with degree <= light_max take the FP32 CTA kernel on the MIXED
+                         path (heavier rows the tensor-core kernel); -1: automatic */
   int32_t hub_min;    /* rows with degree >= hub_min are split across CTAs; -1: automatic */
+  int32_t tiny_max;   /* rows with degree <= tiny_max take the rank-one kernel (BINNED and
+                         MIXED paths); -1: automatic */
+  int32_t autotune;   /* 1: bpmf_init times candidate thresholds for every automatic (-1)
+                         one on this GPU and keeps the fastest; 0: fixed defaults */
 } bpmf_config;
 
 /* Fills `cfg` with the defaults: path MIXED, alpha 2, beta0 2, nu0 K,
- * mu0 = 0, W0 = I, seed 0, order 0, burnin 0, automatic thresholds. */
+ * mu0 = 0, W0 = I, seed 0, order 0, burnin 0, automatic thresholds,
+ * autotune 0 (fixed defaults: the kernel choice, hence the FP32 rounding of
+ * every draw, does not depend on timings). */
 BPMF_API void bpmf_config_default(bpmf_config *cfg, int32_t K);
 
 /* Creates a sampler for the M x N training ratings given as nnz triples
@@ -182,9 +190,20 @@ BPMF_API int bpmf_get_structure(bpmf_t *h, int side, int64_t *ptr, int32_t *idx,
  * Errors: EINVAL, ESTATE, ECUDA. */
 BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
 
-/* Work counters of the last sweep of `side`: rows per bin
- * [tiny, light, heavy, hub] and the number of rows redone in FP64. */
+/* Work counters of `side`: rows per degree bin [tiny, light, heavy, hub]
+ * (tiny: degree <= tiny_max, rank-one updates of chol(Lambda_s), one warp
+ * per row; light: degree <= light_max, FP32 Gram, one CTA per row; heavy:
+ * tensor-core Gram on the MIXED path; hub: degree >= hub_min, split across
+ * CTAs) and the number of rows the last sweep redid in FP64 (paper Sec. IV-B:
+ * a cheap kernel for rows with few ratings, split tasks for rows with many).
+ * Errors: EINVAL. */
 BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *fp64_rows);
+
+/* The degree thresholds in effect for `side`: thresholds[0] = tiny_max
+ * (-1: no rank-one bin), [1] = light_max, [2] = hub_min -- the configured
+ * values, the defaults (tiny_max 0 on the BINNED and MIXED paths, light_max =
+ * tiny_max, hub_min 8192) or the autotuned ones.  Errors: EINVAL. */
+BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[3]);
 
 /* ---- kernel timers (bpmf_get_timing) ---- */
 #define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */
@@ -234,6 +253,67 @@ BPMF_API const char *bpmf_strerror(int code);
 
 /* Detail of the last failure on this host thread ("" if none). */
 BPMF_API const char *bpmf_last_error(void);
+
+/* ---- job server: continuous batching of independent samplers ----------
+ * The paper has no counterpart (it runs one chain on a whole machine).  A
+ * server runs many independent BPMF jobs on the current GPU: jobs wait in
+ * arrival order; the head of the queue is admitted as soon as fewer than
+ * `max_resident` jobs are resident and its device footprint (an upper
+ * estimate of what bpmf_init and its iterations hold) fits in the memory
+ * budget; each admitted job gets its own stream and sampler, and a worker
+ * thread keeps a few of its Gibbs iterations (bpmf_step's graph) queued, so
+ * the kernels of all resident jobs overlap on the device.  When a job's
+ * iterations are done its RMSE and optionally its factors are read back and
+ * its memory is released, which admits the next job.  A job's draws depend
+ * only on its own data, configuration and seed, so its result is bitwise the
+ * same alone and in any mix (with autotune off). */
+typedef struct bpmf_server bpmf_server_t;
+
+typedef struct {
+  int64_t M, N, nnz;        /* training ratings: host triples, copied at submission */
+  const int32_t *row, *col;
+  const float *val;
+  int64_t n_test;           /* held-out triples (host, copied), may be 0 */
+  const int32_t *test_row, *test_col;
+  const float *test_val;
+  bpmf_config cfg;          /* as for bpmf_init; mu0 and W0 are copied at submission */
+  int32_t iterations;       /* Gibbs iterations to run, >= 1 */
+  float *U_out, *V_out;     /* optional host buffers (M*K, N*K floats) written at completion;
+                               they must stay valid until the job is reported done */
+} bpmf_job;
+
+typedef struct {
+  int32_t status;           /* BPMF_OK or the job's first error (ENOMEM: over the budget) */
+  int32_t iterations;       /* iterations run */
+  double rmse_sample;       /* test RMSE of the last sample, NaN without a test set */
+  double rmse_mean;         /* test RMSE of the running mean after burn-in, NaN if none */
+  double t_submit, t_start, t_end;  /* seconds on the server clock: submitted, admitted, done */
+  int64_t device_bytes;     /* budget charged while resident */
+} bpmf_job_result;
+
+/* Starts a server on the current device.  budget_bytes <= 0 selects 0.8 x the
+ * free device memory; max_resident <= 0 selects 16.  Errors: EINVAL, ECUDA. */
+BPMF_API int bpmf_server_create(bpmf_server_t **out, int64_t budget_bytes, int32_t max_resident);
+
+/* Queues a job (any host thread); *id identifies it.  Errors: EINVAL (shape,
+ * K, iterations, missing arrays), ENOMEM (host copy), ESTATE (server stopping). */
+BPMF_API int bpmf_server_submit(bpmf_server_t *s, const bpmf_job *job, int64_t *id);
+
+/* BPMF_OK with *res filled once job `id` is done, EBUSY before.  Errors: EINVAL. */
+BPMF_API int bpmf_server_poll(bpmf_server_t *s, int64_t id, bpmf_job_result *res);
+
+/* Blocks until job `id` is done, then fills *res.  Errors: EINVAL. */
+BPMF_API int bpmf_server_wait(bpmf_server_t *s, int64_t id, bpmf_job_result *res);
+
+/* stats[6] = queued, resident, done, peak resident, peak budgeted bytes, budget.
+ * Errors: EINVAL. */
+BPMF_API int bpmf_server_stats(bpmf_server_t *s, int64_t stats[6]);
+
+/* Seconds since the server started (the clock of bpmf_job_result). */
+BPMF_API double bpmf_server_clock(bpmf_server_t *s);
+
+/* Finishes every submitted job, stops the worker and frees the server. */
+BPMF_API void bpmf_server_destroy(bpmf_server_t *s);
 
 #ifdef __cplusplus
 }

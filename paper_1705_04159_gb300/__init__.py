@@ -20,12 +20,14 @@ __all__ = [
     "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict", "bpmf_test_rmse",
     "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
     "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
-    "bpmf_hyper_stats_noalloc", "bpmf_set_graph",
-    "Sampler", "TIMERS",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds",
+    "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
+    "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
+    "Sampler", "Server", "Job", "JobResult", "TIMERS",
     "USERS", "MOVIES", "PATH_PLAIN", "PATH_BINNED", "PATH_MIXED", "DEVPTR",
 ]
 
-OK, EINVAL, ENOMEM, ECUDA, ENOTPD, ERNG, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ENOTPD, ERNG, ESTATE, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 USERS, MOVIES = 0, 1
 PATH_PLAIN, PATH_BINNED, PATH_MIXED = 0, 1, 2
 DEVPTR = 1
@@ -35,7 +37,9 @@ SYMBOLS = [
     "bpmf_step", "bpmf_predict", "bpmf_test_rmse", "bpmf_get_state", "bpmf_set_state",
     "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
     "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
-    "bpmf_hyper_stats_noalloc", "bpmf_set_graph",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds",
+    "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
+    "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
 ]
 TIMERS = ["hyper_reduce", "hyper_draw", "rows_users", "rows_movies", "fp64_redo", "predict"]
 
@@ -55,8 +59,31 @@ class Config(C.Structure):
         ("K", C.c_int32), ("path", C.c_int32), ("alpha", C.c_double), ("beta0", C.c_double),
         ("nu0", C.c_double), ("mu0", C.c_void_p), ("W0", C.c_void_p), ("seed", C.c_uint64),
         ("order", C.c_int32), ("burnin", C.c_int32), ("light_max", C.c_int32),
-        ("hub_min", C.c_int32),
+        ("hub_min", C.c_int32), ("tiny_max", C.c_int32), ("autotune", C.c_int32),
     ]
+
+
+class Job(C.Structure):
+    """bpmf_job: one server job (host arrays are copied at submission)."""
+    _fields_ = [
+        ("M", C.c_int64), ("N", C.c_int64), ("nnz", C.c_int64),
+        ("row", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+        ("n_test", C.c_int64), ("test_row", C.c_void_p), ("test_col", C.c_void_p),
+        ("test_val", C.c_void_p), ("cfg", Config), ("iterations", C.c_int32),
+        ("U_out", C.c_void_p), ("V_out", C.c_void_p),
+    ]
+
+
+class JobResult(C.Structure):
+    """bpmf_job_result."""
+    _fields_ = [
+        ("status", C.c_int32), ("iterations", C.c_int32), ("rmse_sample", C.c_double),
+        ("rmse_mean", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+        ("t_end", C.c_double), ("device_bytes", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None
@@ -94,10 +121,20 @@ def lib():
         L.bpmf_get_sweep_info.argtypes = [P, C.c_int, P, P]
         L.bpmf_set_timing.argtypes = [P, C.c_int]
         L.bpmf_set_graph.argtypes = [P, C.c_int]
+        L.bpmf_get_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
         L.bpmf_hyper_stats_noalloc.argtypes = [P, i64, i32, P, P, P]
         L.bpmf_destroy.argtypes = [P]
         L.bpmf_destroy.restype = None
+        L.bpmf_server_create.argtypes = [C.POINTER(C.c_void_p), i64, i32]
+        L.bpmf_server_submit.argtypes = [P, C.POINTER(Job), C.POINTER(C.c_int64)]
+        L.bpmf_server_poll.argtypes = [P, i64, C.POINTER(JobResult)]
+        L.bpmf_server_wait.argtypes = [P, i64, C.POINTER(JobResult)]
+        L.bpmf_server_stats.argtypes = [P, P]
+        L.bpmf_server_clock.argtypes = [P]
+        L.bpmf_server_clock.restype = C.c_double
+        L.bpmf_server_destroy.argtypes = [P]
+        L.bpmf_server_destroy.restype = None
         L.bpmf_strerror.argtypes = [C.c_int]
         L.bpmf_strerror.restype = C.c_char_p
         L.bpmf_last_error.argtypes = []
@@ -278,6 +315,13 @@ def bpmf_set_timing(h, enable=True):
     _check(lib().bpmf_set_timing(h, 1 if enable else 0), "bpmf_set_timing")
 
 
+def bpmf_get_thresholds(h, side):
+    """(tiny_max, light_max, hub_min) in effect for `side`."""
+    t = np.zeros(3, np.int64)
+    _check(lib().bpmf_get_thresholds(h, side, t.ctypes.data), "bpmf_get_thresholds")
+    return tuple(int(x) for x in t)
+
+
 def bpmf_set_graph(h, enable=True):
     _check(lib().bpmf_set_graph(h, 1 if enable else 0), "bpmf_set_graph")
 
@@ -310,6 +354,51 @@ def bpmf_destroy(h):
         lib().bpmf_destroy(h)
 
 
+def bpmf_server_create(budget_bytes=0, max_resident=0):
+    h = C.c_void_p()
+    _check(lib().bpmf_server_create(C.byref(h), int(budget_bytes), int(max_resident)),
+           "bpmf_server_create")
+    return h
+
+
+def bpmf_server_submit(srv, job):
+    jid = C.c_int64()
+    _check(lib().bpmf_server_submit(srv, C.byref(job), C.byref(jid)), "bpmf_server_submit")
+    return jid.value
+
+
+def bpmf_server_poll(srv, jid):
+    """The JobResult once job `jid` is done, else None."""
+    r = JobResult()
+    rc = lib().bpmf_server_poll(srv, int(jid), C.byref(r))
+    if rc == EBUSY:
+        return None
+    _check(rc, "bpmf_server_poll")
+    return r
+
+
+def bpmf_server_wait(srv, jid):
+    r = JobResult()
+    _check(lib().bpmf_server_wait(srv, int(jid), C.byref(r)), "bpmf_server_wait")
+    return r
+
+
+def bpmf_server_stats(srv):
+    st = np.zeros(6, np.int64)
+    _check(lib().bpmf_server_stats(srv, st.ctypes.data), "bpmf_server_stats")
+    return dict(zip(("queued", "resident", "done", "peak_resident", "peak_bytes", "budget"),
+                    st.tolist()))
+
+
+def bpmf_server_clock(srv):
+    return lib().bpmf_server_clock(srv)
+
+
+def bpmf_server_destroy(srv):
+    if srv:
+        lib().bpmf_server_destroy(srv)
+
+
 # -------------------------------------------------------------- wrapper --
 
 class Sampler:
@@ -317,7 +406,7 @@ class Sampler:
 
     def __init__(self, M, N, row, col, val, K, alpha=2.0, beta0=2.0, nu0=None, mu0=None, W0=None,
                  seed=0, path=PATH_MIXED, order=0, burnin=0, light_max=-1, hub_min=-1,
-                 stream=None):
+                 tiny_max=-1, autotune=0, stream=None):
         cfg = bpmf_config_default(K)
         cfg.alpha = float(alpha)
         cfg.beta0 = float(beta0)
@@ -328,6 +417,8 @@ class Sampler:
         cfg.burnin = int(burnin)
         cfg.light_max = int(light_max)
         cfg.hub_min = int(hub_min)
+        cfg.tiny_max = int(tiny_max)
+        cfg.autotune = int(autotune)
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.nnz = int(len(row))
         self.h = bpmf_init(M, N, row, col, val, cfg, stream=stream, mu0=mu0, W0=W0)
@@ -392,6 +483,9 @@ class Sampler:
     def set_graph(self, enable=True):
         bpmf_set_graph(self.h, enable)
 
+    def thresholds(self, side):
+        return bpmf_get_thresholds(self.h, side)
+
     def hyper(self):
         """(Lambda_U, mu_U, Lambda_V, mu_V) from the packed state."""
         K = self.K
@@ -400,3 +494,78 @@ class Sampler:
         o = K * K + K
         return (hy[:K * K].reshape(K, K), hy[K * K:o], hy[o:o + K * K].reshape(K, K),
                 hy[o + K * K:])
+
+
+class Server:
+    """Continuous-batching job server on the current CUDA device (bpmf_server_*)."""
+
+    def __init__(self, budget_bytes=0, max_resident=0):
+        self.h = bpmf_server_create(budget_bytes, max_resident)
+        self._outs = {}
+
+    def submit(self, M, N, row, col, val, K, iterations, test=None, alpha=2.0, seed=0,
+               path=PATH_MIXED, burnin=0, want_factors=False, **cfg_kw):
+        """Queues a job; returns its id.  Arrays are host numpy arrays, copied
+        by the call.  With want_factors the final U, V come back from result()."""
+        cfg = bpmf_config_default(K)
+        cfg.alpha = float(alpha)
+        cfg.seed = int(seed)
+        cfg.path = int(path)
+        cfg.burnin = int(burnin)
+        for k, v in cfg_kw.items():
+            setattr(cfg, k, v)
+        row = np.ascontiguousarray(row, np.int32)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float32)
+        j = Job()
+        j.M, j.N, j.nnz = int(M), int(N), len(row)
+        j.row, j.col, j.val = row.ctypes.data, col.ctypes.data, val.ctypes.data
+        keep = [row, col, val]
+        if test is not None:
+            tr, tc, tv = (np.ascontiguousarray(test[0], np.int32),
+                          np.ascontiguousarray(test[1], np.int32),
+                          np.ascontiguousarray(test[2], np.float32))
+            j.n_test = len(tr)
+            j.test_row, j.test_col, j.test_val = tr.ctypes.data, tc.ctypes.data, tv.ctypes.data
+            keep += [tr, tc, tv]
+        j.cfg = cfg
+        j.iterations = int(iterations)
+        outs = None
+        if want_factors:
+            outs = (np.empty((M, K), np.float32), np.empty((N, K), np.float32))
+            j.U_out, j.V_out = outs[0].ctypes.data, outs[1].ctypes.data
+        jid = bpmf_server_submit(self.h, j)
+        del keep  # copied by the call
+        self._outs[jid] = outs
+        return jid
+
+    def poll(self, jid):
+        return bpmf_server_poll(self.h, jid)
+
+    def result(self, jid):
+        """(JobResult, (U, V) or None), waiting for the job."""
+        r = bpmf_server_wait(self.h, jid)
+        return r, self._outs.pop(jid, None)
+
+    def stats(self):
+        return bpmf_server_stats(self.h)
+
+    def clock(self):
+        return bpmf_server_clock(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            bpmf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

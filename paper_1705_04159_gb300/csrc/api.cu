@@ -54,7 +54,7 @@ void free_handle(Handle* h) {
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhl);
-    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.xbar); dfree(sd.S);
+    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.lchol); dfree(sd.xbar); dfree(sd.S);
     dfree(sd.piece_row); dfree(sd.piece_e0); dfree(sd.piece_e1); dfree(sd.hub_piece0);
   }
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
@@ -76,6 +76,8 @@ int to_device(const T* src, int64_t n, bool devptr, T** dst, bool* owned, cudaSt
   BPMF_CUDA_CHECK(cudaMemcpyAsync(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice, st));
   return BPMF_OK;
 }
+
+}  // namespace
 
 // Reads and clears the device status word; maps bits to a status code.
 int check_status(Handle* h, const char* where) {
@@ -101,6 +103,8 @@ int check_status(Handle* h, const char* where) {
   }
   return BPMF_OK;
 }
+
+namespace {
 
 int valid_side(int side) { return side == BPMF_USERS || side == BPMF_MOVIES; }
 
@@ -185,6 +189,28 @@ int capture_step(Handle* h) {
   return BPMF_OK;
 }
 
+}  // namespace
+
+// Queues one Gibbs iteration on the handle's stream without waiting for it.
+int step_async(Handle* h) {
+  if (h->use_graph) {
+    if (h->graph && h->graph_timing != h->timing) drop_graph(h);
+    if (!h->graph) BPMF_TRY(capture_step(h));
+    BPMF_CUDA_CHECK(cudaGraphLaunch(h->graph, h->stream));
+    h->kernels += h->graph_kernels;
+  } else {
+    BPMF_TRY(step_body(h));
+  }
+  if (h->n_test > 0) {
+    if (h->iter >= h->cfg.burnin) h->n_avg += 1;
+    h->have_rmse = true;
+  }
+  h->iter += 1;
+  return BPMF_OK;
+}
+
+namespace {
+
 // Adds the phase times of the last replay (the stream is idle).
 int resolve_graph_timers(Handle* h) {
   for (auto& p : h->graph_timers) {
@@ -218,6 +244,8 @@ void bpmf_config_default(bpmf_config* c, int32_t K) {
   c->burnin = 0;
   c->light_max = -1;
   c->hub_min = -1;
+  c->tiny_max = -1;
+  c->autotune = 0;
 }
 
 const char* bpmf_strerror(int code) {
@@ -229,6 +257,7 @@ const char* bpmf_strerror(int code) {
     case BPMF_ENOTPD: return "matrix not positive definite";
     case BPMF_ERNG: return "random sampler rejection cap reached";
     case BPMF_ESTATE: return "call out of order";
+    case BPMF_EBUSY: return "not finished yet";
     default: return "unknown status";
   }
 }
@@ -288,6 +317,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       if ((rc = dalloc(&sd.lam, KK))) break;
       if ((rc = dalloc(&sd.mu, K))) break;
       if ((rc = dalloc(&sd.lamaug, (int64_t)(K + 1) * (K + 1)))) break;
+      if ((rc = dalloc(&sd.lchol, KK))) break;
       if ((rc = dalloc(&sd.xbar, K))) break;
       if ((rc = dalloc(&sd.S, KK))) break;
     }
@@ -349,6 +379,16 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     if ((rc = setup_bins(h, BPMF_MOVIES))) break;
     if ((rc = launch_init_factors(h, BPMF_USERS))) break;
     if ((rc = launch_init_factors(h, BPMF_MOVIES))) break;
+    if (cfg->autotune) {
+      float* scratch = nullptr;
+      if ((rc = dalloc(&scratch, std::max(M, N) * K))) break;
+      rc = autotune_bins(h, BPMF_USERS, scratch);
+      if (rc == BPMF_OK) rc = autotune_bins(h, BPMF_MOVIES, scratch);
+      cudaStreamSynchronize(h->stream);
+      dfree(scratch);
+      if (rc == BPMF_OK) rc = check_status(h, "bpmf_init (autotune)");
+      if (rc) break;
+    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
       set_error("bpmf_init: %s", cudaGetErrorString(cudaGetLastError()));
       rc = BPMF_ECUDA;
@@ -444,19 +484,7 @@ int bpmf_sweep(bpmf_t* hh, int side) {
 int bpmf_step(bpmf_t* hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return BPMF_EINVAL;
-  if (h->use_graph) {
-    if (h->graph && h->graph_timing != h->timing) drop_graph(h);
-    if (!h->graph) BPMF_TRY(capture_step(h));
-    BPMF_CUDA_CHECK(cudaGraphLaunch(h->graph, h->stream));
-    h->kernels += h->graph_kernels;
-  } else {
-    BPMF_TRY(step_body(h));
-  }
-  if (h->n_test > 0) {
-    if (h->iter >= h->cfg.burnin) h->n_avg += 1;
-    h->have_rmse = true;
-  }
-  h->iter += 1;
+  BPMF_TRY(step_async(h));
   const int rc = check_status(h, "bpmf_step");
   if (rc == BPMF_OK && h->use_graph && h->timing) BPMF_TRY(resolve_graph_timers(h));
   return rc;
@@ -558,7 +586,8 @@ int bpmf_set_state(bpmf_t* hh, const float* U, const float* V, const double* hyp
                                       cudaMemcpyHostToDevice, h->stream));
       BPMF_CUDA_CHECK(cudaMemcpyAsync(h->side[s].mu, base + KK, sizeof(double) * K,
                                       cudaMemcpyHostToDevice, h->stream));
-      BPMF_TRY(launch_check_spd_f64(h->side[s].lam, K, h->wscr, h->status, h->stream));
+      BPMF_TRY(launch_check_spd_f64(h->side[s].lam, K, h->wscr, h->status, h->side[s].lchol,
+                                    h->stream));
       BPMF_TRY(launch_hyper_to_f32(h, s));
     }
     const int rc = check_status(h, "bpmf_set_state");
@@ -601,6 +630,16 @@ int bpmf_get_hyper_stats(bpmf_t* hh, int side, double* xbar, double* S) {
   if (xbar) BPMF_CUDA_CHECK(cudaMemcpyAsync(xbar, sd.xbar, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
   if (S) BPMF_CUDA_CHECK(cudaMemcpyAsync(S, sd.S, sizeof(double) * K * K, cudaMemcpyDeviceToHost, h->stream));
   BPMF_CUDA_CHECK(cudaStreamSynchronize(h->stream));
+  return BPMF_OK;
+}
+
+int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[3]) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !valid_side(side) || !thresholds) return BPMF_EINVAL;
+  const SideDev& sd = h->side[side];
+  thresholds[0] = sd.tiny_max;
+  thresholds[1] = sd.light_max;
+  thresholds[2] = sd.hub_min;
   return BPMF_OK;
 }
 

@@ -1,16 +1,23 @@
-// binned.cu -- degree-binned half-sweep.
+// binned.cu -- degree-binned half-sweep and the threshold autotuner.
 //
-// The paper (Sec. III) keeps its cores busy by giving rows with few ratings
-// a cheap serial kernel and by splitting rows with many ratings (>= 1000 on
-// its CPUs) into smaller tasks.  Here each side's rows are visited in degree
-// order (largest first, ties by row id), so every bin is a contiguous slice
-// of that order and the heaviest work starts first:
-//   hubs  (degree >= hub_min): split into pieces of min(kPiece, hub_min / 2)
-//         ratings; one CTA
-//         per piece computes a partial Gram, then one CTA per hub sums its
-//         partials in piece order (deterministic) and factorises;
-//   other rows: one CTA per row, Gram from its ratings.
-// Rows with degree 0 take the same kernel (their Gram is empty: a prior draw).
+// The paper (Sec. III, IV-B) keeps its cores busy by giving rows with few
+// ratings a cheap serial kernel and by splitting rows with many ratings
+// (>= 1000 on its CPUs) into smaller tasks; its workload model is a fixed
+// cost per row plus a cost per rating.  Here each side's rows are visited in
+// degree order (largest first, ties by row id), so every bin is a contiguous
+// slice of that order and, inside each launch, the heaviest rows start first
+// (CTAs are issued in index order: a longest-first greedy schedule):
+//   hub   (degree >= hub_min): split into pieces of min(kPiece, hub_min / 2)
+//         ratings; one CTA per piece computes a partial Gram, then one CTA per
+//         hub sums its partials in piece order (deterministic) and factorises;
+//   heavy (light_max < degree < hub_min): one CTA per row, tensor-core Gram
+//         on the MIXED path, FP32 Gram otherwise;
+//   light (tiny_max < degree <= light_max): one CTA per row, FP32 Gram;
+//   tiny  (degree <= tiny_max, degree 0 included): one warp per row, rank-one
+//         updates of chol(Lambda_s) (rank1.cu).
+// The thresholds are fixed by the configuration, or by defaults, or -- with
+// autotune on -- by timing candidate values on this GPU and this degree
+// histogram at initialisation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,50 +34,56 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   SweepArgs a = a0;
   a.rows = sd.perm;
   const bool tc = h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K);
+  const int64_t e_hub = sd.n_hub;
+  const int64_t e_heavy = e_hub + sd.bin_count[kBinHeavy];
+  const int64_t e_light = e_heavy + sd.bin_count[kBinLight];
   if (sd.n_hub > 0) {
     if (tc) BPMF_TRY(launch_pieces_tc(a, sd.n_pieces, h->status, st, &h->kernels));
     else BPMF_TRY(launch_pieces_fp32(a, sd.n_pieces, st, &h->kernels));
     SweepArgs f = a;
     f.row_begin = 0;
-    f.row_end = sd.n_hub;
+    f.row_end = e_hub;
     BPMF_TRY(launch_hub_finish_fp32(f, st, &h->kernels));
   }
-  a.row_begin = sd.n_hub;
-  a.row_end = sd.R;
-  if (tc) return launch_rows_tc(a, h->status, st, &h->kernels);
-  return launch_rows_fp32(a, st, &h->kernels);
+  SweepArgs r = a;
+  if (tc) {
+    r.row_begin = e_hub;
+    r.row_end = e_heavy;
+    BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
+    r.row_begin = e_heavy;
+    r.row_end = e_light;
+    BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
+  } else {
+    r.row_begin = e_hub;
+    r.row_end = e_light;
+    BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
+  }
+  r.row_begin = e_light;
+  r.row_end = sd.R;
+  return launch_rows_rank1(r, sd.lchol, st, &h->kernels);
 }
 
-// Degree thresholds of one side and the pieces of its hubs.  Bins (for the
-// counters): tiny = degree 0, light = 1..light_max, heavy = up to hub_min-1,
-// hub = hub_min and above.  Piece construction is host logic on the degree
-// order, done once per sampler.
-int setup_bins(Handle* h, int s) {
+namespace {
+
+// Row counts per bin and the pieces of the hubs for the given thresholds.
+int apply_bins(Handle* h, int s, int64_t tiny_max, int64_t light_max, int64_t hub_min) {
   SideDev& sd = h->side[s];
   cudaStream_t st = h->stream;
   const int64_t R = sd.R;
-  std::vector<int64_t> ptr(R + 1);
-  std::vector<int32_t> perm(R);
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(ptr.data(), sd.ptr, sizeof(int64_t) * (R + 1),
-                                  cudaMemcpyDeviceToHost, st));
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(perm.data(), sd.perm, sizeof(int32_t) * R,
-                                  cudaMemcpyDeviceToHost, st));
-  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
-  sd.light_max = h->cfg.light_max >= 0 ? h->cfg.light_max : 0;
-  sd.hub_min = h->cfg.hub_min >= 0 ? std::max<int64_t>(1, h->cfg.hub_min) : 2 * kPiece;
+  hub_min = std::max<int64_t>(1, hub_min);
+  light_max = std::max(light_max, tiny_max);
+  const bool new_hubs = hub_min != sd.hub_min || sd.hub_piece0 == nullptr;
+  sd.tiny_max = tiny_max;
+  sd.light_max = light_max;
+  sd.hub_min = hub_min;
   for (int b = 0; b < kNumBins; ++b) sd.bin_count[b] = 0;
-  // piece length: half the hub threshold, at most kPiece ratings
-  const int64_t plen = std::max<int64_t>(1, std::min<int64_t>(kPiece, sd.hub_min / 2));
   int64_t n_hub = 0;
-  std::vector<int32_t> prow, hub0;
-  std::vector<int64_t> pe0, pe1;
   for (int64_t q = 0; q < R; ++q) {
-    const int32_t r = perm[q];
-    const int64_t d = ptr[r + 1] - ptr[r];
+    const int64_t d = sd.deg_h[q];
     int bin;
-    if (d >= sd.hub_min) bin = kBinHub;
-    else if (d == 0) bin = kBinTiny;
-    else if (d <= sd.light_max) bin = kBinLight;
+    if (d >= hub_min) bin = kBinHub;
+    else if (d <= tiny_max) bin = kBinTiny;
+    else if (d <= light_max) bin = kBinLight;
     else bin = kBinHeavy;
     sd.bin_count[bin] += 1;
     if (bin == kBinHub) {
@@ -79,37 +92,50 @@ int setup_bins(Handle* h, int s) {
         set_error("setup_bins: degree order is not monotone");
         return BPMF_ECUDA;
       }
-      hub0.push_back((int32_t)prow.size());
-      for (int64_t e = ptr[r]; e < ptr[r + 1]; e += plen) {
-        prow.push_back(r);
-        pe0.push_back(e);
-        pe1.push_back(std::min(ptr[r + 1], e + plen));
-      }
       ++n_hub;
     }
   }
+  if (!new_hubs) return BPMF_OK;
+  // piece length: half the hub threshold, at most kPiece ratings
+  const int64_t plen = std::max<int64_t>(1, std::min<int64_t>(kPiece, hub_min / 2));
+  std::vector<int32_t> prow, hub0;
+  std::vector<int64_t> pe0, pe1;
+  for (int64_t q = 0; q < n_hub; ++q) {
+    const int32_t r = sd.perm_h[q];
+    hub0.push_back((int32_t)prow.size());
+    for (int64_t e = sd.ptr_h[r]; e < sd.ptr_h[r + 1]; e += plen) {
+      prow.push_back(r);
+      pe0.push_back(e);
+      pe1.push_back(std::min(sd.ptr_h[r + 1], e + plen));
+    }
+  }
   hub0.push_back((int32_t)prow.size());
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
+  cudaFree(sd.piece_row);
+  cudaFree(sd.piece_e0);
+  cudaFree(sd.piece_e1);
+  cudaFree(sd.hub_piece0);
+  sd.piece_row = nullptr;
+  sd.piece_e0 = sd.piece_e1 = nullptr;
+  sd.hub_piece0 = nullptr;
   sd.n_hub = n_hub;
   sd.n_pieces = (int64_t)prow.size();
+  const int64_t np = std::max<int64_t>(1, sd.n_pieces);
+  BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_row, sizeof(int32_t) * np));
+  BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_e0, sizeof(int64_t) * np));
+  BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_e1, sizeof(int64_t) * np));
+  BPMF_CUDA_CHECK(cudaMalloc(&sd.hub_piece0, sizeof(int32_t) * (n_hub + 1)));
   if (sd.n_pieces > 0) {
-    cudaFree(sd.piece_row);
-    cudaFree(sd.piece_e0);
-    cudaFree(sd.piece_e1);
-    cudaFree(sd.hub_piece0);
-    BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_row, sizeof(int32_t) * sd.n_pieces));
-    BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_e0, sizeof(int64_t) * sd.n_pieces));
-    BPMF_CUDA_CHECK(cudaMalloc(&sd.piece_e1, sizeof(int64_t) * sd.n_pieces));
-    BPMF_CUDA_CHECK(cudaMalloc(&sd.hub_piece0, sizeof(int32_t) * (n_hub + 1)));
     BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.piece_row, prow.data(), sizeof(int32_t) * sd.n_pieces,
                                     cudaMemcpyHostToDevice, st));
     BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.piece_e0, pe0.data(), sizeof(int64_t) * sd.n_pieces,
                                     cudaMemcpyHostToDevice, st));
     BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.piece_e1, pe1.data(), sizeof(int64_t) * sd.n_pieces,
                                     cudaMemcpyHostToDevice, st));
-    BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.hub_piece0, hub0.data(), sizeof(int32_t) * (n_hub + 1),
-                                    cudaMemcpyHostToDevice, st));
-    BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
   }
+  BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.hub_piece0, hub0.data(), sizeof(int32_t) * (n_hub + 1),
+                                  cudaMemcpyHostToDevice, st));
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
   // one partial buffer serves both sides (the sweeps run one after the other)
   const int64_t need = sd.n_pieces * partial_floats_per_piece(h->K);
   if (need > h->hub_part_len) {
@@ -118,6 +144,148 @@ int setup_bins(Handle* h, int s) {
     BPMF_CUDA_CHECK(cudaMalloc(&h->hub_part, sizeof(float) * need));
     h->hub_part_len = need;
   }
+  return BPMF_OK;
+}
+
+int64_t default_tiny_max(const Handle* h) { return h->cfg.path == BPMF_PATH_PLAIN ? -1 : 0; }
+
+}  // namespace
+
+// Host copies of the degree order and the thresholds in effect.
+int setup_bins(Handle* h, int s) {
+  SideDev& sd = h->side[s];
+  cudaStream_t st = h->stream;
+  const int64_t R = sd.R;
+  sd.ptr_h.assign(R + 1, 0);
+  sd.perm_h.assign(R, 0);
+  sd.deg_h.assign(R, 0);
+  BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.ptr_h.data(), sd.ptr, sizeof(int64_t) * (R + 1),
+                                  cudaMemcpyDeviceToHost, st));
+  BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.perm_h.data(), sd.perm, sizeof(int32_t) * R,
+                                  cudaMemcpyDeviceToHost, st));
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
+  for (int64_t q = 0; q < R; ++q) {
+    const int32_t r = sd.perm_h[q];
+    sd.deg_h[q] = sd.ptr_h[r + 1] - sd.ptr_h[r];
+  }
+  sd.hub_min = 0;  // forces the pieces to be built
+  const int64_t tiny = h->cfg.tiny_max >= 0 ? h->cfg.tiny_max : default_tiny_max(h);
+  const int64_t light = h->cfg.light_max >= 0 ? h->cfg.light_max : tiny;
+  const int64_t hub = h->cfg.hub_min >= 0 ? h->cfg.hub_min : 2 * kPiece;
+  return apply_bins(h, s, tiny, light, hub);
+}
+
+// ---------------------------------------------------------------- autotune --
+// Each automatic threshold is chosen by timing one half-sweep of the side per
+// candidate (hyperparameters drawn from the initial factors, output written
+// to scratch so that the sampler state is untouched), one threshold after the
+// other: hub_min, then light_max (MIXED path), then tiny_max.  The fastest
+// candidate stays.  Timings come from CUDA events around the sweep's launches.
+namespace {
+
+int time_sweep(Handle* h, int s, float* scratch, int reps, float* best_ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BPMF_CUDA_CHECK(cudaEventCreate(&e0));
+  BPMF_CUDA_CHECK(cudaEventCreate(&e1));
+  int rc = BPMF_OK;
+  float best = 3.0e38f;
+  for (int r = 0; r <= reps && rc == BPMF_OK; ++r) {  // the first run warms up
+    SweepArgs a = make_sweep_args(h, s);
+    a.X = scratch;
+    if (cudaMemsetAsync(h->flag_count, 0, sizeof(int32_t), h->stream) != cudaSuccess ||
+        cudaEventRecord(e0, h->stream) != cudaSuccess)
+      rc = BPMF_ECUDA;
+    if (rc == BPMF_OK) {
+      if (h->cfg.path == BPMF_PATH_PLAIN) rc = launch_rows_fp32(a, h->stream, &h->kernels);
+      else rc = launch_sweep_binned(h, s, a);
+    }
+    if (rc == BPMF_OK && cudaEventRecord(e1, h->stream) != cudaSuccess) rc = BPMF_ECUDA;
+    if (rc == BPMF_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = BPMF_ECUDA;
+    float ms = 0.f;
+    if (rc == BPMF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BPMF_ECUDA;
+    if (rc == BPMF_OK && r > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == BPMF_ECUDA) set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+  *best_ms = best;
+  return rc;
+}
+
+// Candidates that change at least one row's bin, largest degree first.
+std::vector<int64_t> distinct_cuts(const SideDev& sd, std::vector<int64_t> c) {
+  std::sort(c.begin(), c.end());
+  c.erase(std::unique(c.begin(), c.end()), c.end());
+  std::vector<int64_t> out;
+  int64_t last_count = -1;
+  for (int64_t v : c) {
+    // rows with degree <= v (deg_h is non-increasing)
+    const int64_t n = (int64_t)(sd.deg_h.end() -
+                                std::upper_bound(sd.deg_h.begin(), sd.deg_h.end(), v,
+                                                 [](int64_t x, int64_t y) { return x > y; }));
+    if (n != last_count) out.push_back(v);
+    last_count = n;
+  }
+  return out;
+}
+
+}  // namespace
+
+int autotune_bins(Handle* h, int s, float* scratch) {
+  SideDev& sd = h->side[s];
+  if (h->cfg.path == BPMF_PATH_PLAIN || sd.R == 0) return BPMF_OK;
+  BPMF_TRY(launch_hyper(h, s));
+  const int reps = 2;
+  float ms = 0.f;
+  const int64_t maxdeg = sd.deg_h.empty() ? 0 : sd.deg_h[0];
+  if (h->cfg.hub_min < 0 && maxdeg >= 2048) {
+    int64_t best_v = sd.hub_min;
+    float best = 3.0e38f;
+    for (int64_t v : {(int64_t)2048, (int64_t)4096, (int64_t)8192, (int64_t)16384,
+                      (int64_t)1 << 40}) {
+      if (v != (int64_t)1 << 40 && v > maxdeg) continue;
+      BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, v));
+      BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, best_v));
+  }
+  if (h->cfg.light_max < 0 && h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K)) {
+    int64_t best_v = sd.light_max;
+    float best = 3.0e38f;
+    for (int64_t v : distinct_cuts(sd, {sd.tiny_max, 8, 16, 32, 64, 128, 256, 512, 1024})) {
+      if (v < sd.tiny_max) continue;
+      BPMF_TRY(apply_bins(h, s, sd.tiny_max, v, sd.hub_min));
+      BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    BPMF_TRY(apply_bins(h, s, sd.tiny_max, best_v, sd.hub_min));
+  }
+  if (h->cfg.tiny_max < 0) {
+    const int64_t light = sd.light_max;
+    int64_t best_v = sd.tiny_max;
+    float best = 3.0e38f;
+    for (int64_t v : distinct_cuts(sd, {-1, 0, 1, 2, 4, 8, 16, 32, 64})) {
+      // a tiny threshold above light_max moves light rows (and the boundary)
+      BPMF_TRY(apply_bins(h, s, v, std::max(light, v), sd.hub_min));
+      BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    BPMF_TRY(apply_bins(h, s, best_v, std::max(light, best_v), sd.hub_min));
+  }
+  // the tuning draws left the side's hyperparameters set; the chain starts
+  // without them, as before tuning
+  sd.have_hyper = false;
+  sd.have_stats = false;
   return BPMF_OK;
 }
 

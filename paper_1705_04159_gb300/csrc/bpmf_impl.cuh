@@ -47,6 +47,7 @@ struct SideDev {
   double* lam = nullptr;   // K*K
   double* mu = nullptr;    // K
   float* lamaug = nullptr; // (K+1)^2: Lambda_s bordered by b0 = Lambda_s mu_s (row and column K)
+  float* lchol = nullptr;  // K(K+1)/2: chol(Lambda_s), lower, packed by rows, FP32 (rank-one kernel)
   // split rows (hubs): pieces of at most kPiece ratings, in degree order
   int64_t n_hub = 0, n_pieces = 0;
   int32_t* piece_row = nullptr;     // [n_pieces] row id
@@ -56,7 +57,10 @@ struct SideDev {
   double* xbar = nullptr;  // K      (last statistics)
   double* S = nullptr;     // K*K
   int64_t bin_count[kNumBins] = {0, 0, 0, 0};  // rows per bin (perm order: hub, heavy, light, tiny)
-  int64_t light_max = 0, hub_min = 0;          // thresholds in effect
+  int64_t tiny_max = -1, light_max = 0, hub_min = 0;  // thresholds in effect
+  std::vector<int64_t> deg_h;   // host: degrees in degree order
+  std::vector<int64_t> ptr_h;   // host: row pointers
+  std::vector<int32_t> perm_h;  // host: degree order
   int64_t max_deg = 0;
   bool have_hyper = false;
   bool have_stats = false;
@@ -214,12 +218,14 @@ int sort_test_set(Handle* h, const int32_t* d_row, const int32_t* d_col, const f
                   int64_t n, uint32_t* keys, uint32_t* keys_sorted, int32_t* ids, int32_t* src);
 int validate_pairs(Handle* h, const int32_t* d_row, const int32_t* d_col, int64_t n);
 int setup_bins(Handle* h, int s);
+int autotune_bins(Handle* h, int s, float* scratch);  // binned.cu
 
 // hyper.cu
 int launch_hyper(Handle* h, int s);
 int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch, int* status,
                            cudaStream_t st);
-int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, cudaStream_t st);
+int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, float* lout,
+                         cudaStream_t st);
 int launch_hyper_to_f32(Handle* h, int s);
 int launch_stats_into(const float* X, int64_t R, int K, double* part, int blocks, double* xbar,
                       double* S, float* xbarf, cudaStream_t st);
@@ -236,6 +242,8 @@ int launch_advance_iter(Handle* h);
 
 // api.cu
 void set_error(const char* fmt, ...);
+int step_async(Handle* h);          // one iteration queued on h->stream, no wait
+int check_status(Handle* h, const char* where);  // waits for the stream, maps device status
 
 }  // namespace gb
 

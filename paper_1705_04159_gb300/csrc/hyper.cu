@@ -279,6 +279,7 @@ struct HyperArgs {
   double* lam;
   double* mu;
   float* lamaug;
+  float* lchol;  // chol(Lambda) = B in FP32, packed by rows, for the rank-one row kernel
   int* status;
 };
 
@@ -325,6 +326,8 @@ __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
     if (j <= i)
       for (int m = j; m <= i; ++m) v += T[(K - 1 - m) * K + (K - 1 - i)] * A[m * K + j];
     B[e] = v;
+    // Lambda = B B^T with B lower, positive diagonal: B = chol(Lambda), packed by rows
+    if (j <= i) a.lchol[i * (i + 1) / 2 + j] = (float)v;
   }
   __syncthreads();
   // Lambda = B B^T (lower triangle, mirrored)
@@ -369,12 +372,21 @@ __global__ void __launch_bounds__(512) spd_inverse_kernel(const double* A, doubl
   cta_ata(Li, Ainv, K);
 }
 
+// Checks that A is SPD; on success writes chol(A) in FP32 to lout (lower
+// triangle packed by rows: element (i, j) at i (i + 1) / 2 + j).
 __global__ void __launch_bounds__(512) spd_check_kernel(const double* A, int K, double* scr,
-                                                        int* status) {
+                                                        int* status, float* lout) {
   __shared__ int bad;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) scr[e] = A[e];
   __syncthreads();
-  if (!cta_cholesky(scr, K, &bad) && threadIdx.x == 0) atomicOr(status, kStatusNotPD);
+  if (!cta_cholesky(scr, K, &bad)) {
+    if (threadIdx.x == 0) atomicOr(status, kStatusNotPD);
+    return;
+  }
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, j = e % K;
+    if (j <= i) lout[i * (i + 1) / 2 + j] = (float)scr[e];
+  }
 }
 
 // float copies of a side's hyperparameters (after bpmf_set_state)
@@ -429,6 +441,7 @@ int launch_hyper(Handle* h, int s) {
   a.lam = sd.lam;
   a.mu = sd.mu;
   a.lamaug = sd.lamaug;
+  a.lchol = sd.lchol;
   a.status = h->status;
   {
     PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
@@ -465,8 +478,9 @@ int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch
   return BPMF_OK;
 }
 
-int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, cudaStream_t st) {
-  spd_check_kernel<<<1, 512, 0, st>>>(A, K, scratch, status);
+int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, float* lout,
+                         cudaStream_t st) {
+  spd_check_kernel<<<1, 512, 0, st>>>(A, K, scratch, status, lout);
   BPMF_CUDA_CHECK(cudaGetLastError());
   return BPMF_OK;
 }

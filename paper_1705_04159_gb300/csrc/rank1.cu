@@ -62,10 +62,13 @@ __device__ __forceinline__ void rank_one_wave(float* L, int K, float (&x)[kR1Wav
         const int owner = k & 31, mk = k >> 5;
         const float xk = __shfl_sync(0xffffffffu, elem<NPL>(x[t], mk), owner);
         const float lkk = L[tri(k) + k];
-        const float r = sqrtf(fmaf(lkk, lkk, xk * xk));
-        const float s = xk / lkk;
-        const float c = r / lkk;
-        const float ic = lkk / r;
+        const float q = fmaf(lkk, lkk, xk * xk);
+        const float rq = rsqrtf(q);
+        const float r = q * rq;       // sqrt(L_kk^2 + x_k^2)
+        const float ic = lkk * rq;    // 1 / c
+        const float il = 1.0f / lkk;
+        const float s = xk * il;
+        const float c = r * il;
 #pragma unroll
         for (int m = 0; m < NPL; ++m) {
           const int i = lane + 32 * m;
@@ -84,8 +87,8 @@ __device__ __forceinline__ void rank_one_wave(float* L, int K, float (&x)[kR1Wav
 }
 
 template <int NPL>
-__global__ void __launch_bounds__(256) row_rank1(const SweepArgs a, const float* __restrict__ lchol,
-                                                 int warps) {
+__global__ void __launch_bounds__(256, 2)
+    row_rank1(const SweepArgs a, const float* __restrict__ lchol, int warps) {
   extern __shared__ __align__(16) float r1s[];
   const int K = a.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -94,8 +97,15 @@ __global__ void __launch_bounds__(256) row_rank1(const SweepArgs a, const float*
   const int row = a.rows ? a.rows[slot] : (int)slot;
   float* L = r1s + warp * r1_floats(K);
   float* zv = L + tri(K);
-  for (int i = 0; i < K; ++i)
-    for (int k = lane; k <= i; k += 32) L[tri(i) + k] = __ldg(lchol + (int64_t)i * K + k);
+  {
+    // chol(Lambda_s) is stored packed like L: one contiguous copy
+    const int n = tri(K), n4 = n >> 2;
+    const float4* src = reinterpret_cast<const float4*>(lchol);
+    float4* dst = reinterpret_cast<float4*>(L);
+#pragma unroll 4
+    for (int e = lane; e < n4; e += 32) dst[e] = __ldg(src + e);
+    for (int e = 4 * n4 + lane; e < n; e += 32) L[e] = __ldg(lchol + e);
+  }
   const uint32_t t = *a.tp;
   for (int q = lane; 4 * q < K; q += 32) {
     const float4 z = normal4_f32(philox(make_uint4((uint32_t)row, t, (uint32_t)q, a.sw), a.key));
@@ -134,10 +144,17 @@ __global__ void __launch_bounds__(256) row_rank1(const SweepArgs a, const float*
     }
     rank_one_wave<NPL>(L, K, x, W, lane);
   }
+  // reciprocal diagonal of the owned rows
+  float rd[NPL];
+#pragma unroll
+  for (int m = 0; m < NPL; ++m) {
+    const int i = lane + 32 * m;
+    rd[m] = i < K ? 1.0f / L[tri(i) + i] : 0.f;
+  }
   // y = L^-1 b, by columns
   for (int k = 0; k < K; ++k) {
     const int owner = k & 31, mk = k >> 5;
-    const float yk = __shfl_sync(0xffffffffu, elem<NPL>(b, mk), owner) / L[tri(k) + k];
+    const float yk = __shfl_sync(0xffffffffu, elem<NPL>(b, mk) * elem<NPL>(rd, mk), owner);
     if (lane == owner) set_elem<NPL>(b, mk, yk);
 #pragma unroll
     for (int m = 0; m < NPL; ++m) {
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(256) row_rank1(const SweepArgs a, const float*
   }
   for (int k = K - 1; k >= 0; --k) {
     const int owner = k & 31, mk = k >> 5;
-    const float uk = __shfl_sync(0xffffffffu, elem<NPL>(b, mk), owner) / L[tri(k) + k];
+    const float uk = __shfl_sync(0xffffffffu, elem<NPL>(b, mk) * elem<NPL>(rd, mk), owner);
     if (lane == owner) set_elem<NPL>(b, mk, uk);
 #pragma unroll
     for (int m = 0; m < NPL; ++m) {

@@ -47,5 +47,7 @@ int launch_rows_tc(const SweepArgs& a, int* status, cudaStream_t st, int64_t* la
 int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStream_t st,
                      int64_t* launches);
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
+// rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
+int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
 
 }  // namespace gb

@@ -28,6 +28,9 @@ Recipes (paper Sec. V-B names the public datasets; only their shapes are used):
   (largest expected column degree 230k, largest expected row degree 8,885),
   value = clip(round(3.6 + u.v + N(0, 1)), 1, 5), planted rank 100.
 * ``powerlaw``: the same Chung-Lu construction at any size (parity cases).
+* ``serving_stream`` / ``serving_job``: a stream of independent jobs with
+  Poisson arrivals (rate 20/s) and log-uniform shapes (rows 1k-200k, columns
+  1k-50k, ratings 10k-5M, K in {16, 32, 64}), uniformly placed cells.
 
 Every recipe holds out 10% of the cells, chosen uniformly, as the test set.
 """
@@ -40,7 +43,7 @@ import os
 import numpy as np
 
 __all__ = ["Dataset", "tiny", "tiny_dense", "movielens", "chembl", "netflix",
-           "powerlaw", "uniform", "make", "RECIPES"]
+           "powerlaw", "uniform", "make", "RECIPES", "serving_stream", "serving_job"]
 
 
 @dataclasses.dataclass
@@ -288,6 +291,61 @@ def netflix(seed: int = 0, device: str = "cpu") -> Dataset:
     parts = _split(rng, r, c, val)
     return Dataset("netflix", M, N, K, 2.0, *parts, clip=(1.0, 5.0),
                    note=f"Netflix shape: row exponent {row_expo:.3f}, column exponent {col_expo:.3f}")
+
+
+def serving_stream(n_jobs: int = 256, rate: float = 20.0, seed: int = 0) -> list:
+    """Arrival times and shapes of a stream of independent jobs.
+
+    Poisson arrivals (exponential gaps of mean 1/rate seconds) from a Philox
+    generator; rows log-uniform in [1k, 200k], columns log-uniform in
+    [1k, 50k], ratings log-uniform in [10k, 5M] capped at rows x cols / 2,
+    K uniform over {16, 32, 64}.  Returns dicts with keys arrival_s, M, N,
+    nnz, K, seed.
+    """
+    rng = np.random.Generator(np.random.Philox(seed))
+    t = 0.0
+    out = []
+    for j in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        M = int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
+        N = int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4)))))
+        nnz = int(round(math.exp(rng.uniform(math.log(1e4), math.log(5e6)))))
+        nnz = min(nnz, M * N // 2)
+        K = int(rng.choice([16, 32, 64]))
+        out.append(dict(arrival_s=t, M=M, N=N, nnz=nnz, K=K, seed=j + 1))
+    return out
+
+
+def serving_job(spec: dict, device: str = "cpu") -> Dataset:
+    """Uniformly placed distinct cells with a planted unit-variance rank-K
+    signal plus N(0, 0.5^2) noise for one job of ``serving_stream``."""
+    M, N, nnz, K = spec["M"], spec["N"], spec["nnz"], spec["K"]
+    rng = np.random.default_rng(spec["seed"])
+    sd = (1.0 / K) ** 0.25
+    U = rng.normal(0.0, sd, size=(M, K))
+    V = rng.normal(0.0, sd, size=(N, K))
+    if device == "cpu":
+        r, c = _uniform_cells(rng, M, N, nnz)
+    else:
+        r, c = _uniform_cells_device(rng, M, N, nnz, device)
+    val = _planted_dot(U, V, r, c, device) + rng.normal(0.0, 0.5, size=r.shape[0])
+    parts = _split(rng, r, c, val.astype(np.float32))
+    return Dataset(f"job_{M}x{N}_{nnz}_K{K}", M, N, K, 4.0, *parts)
+
+
+def _uniform_cells_device(rng, M, N, nnz, device):
+    """``nnz`` distinct cells uniformly at random (torch on ``device``)."""
+    torch = _torch()
+    g = torch.Generator(device=device)
+    g.manual_seed(int(rng.integers(0, 2 ** 62)))
+    total = M * N
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    while keys.numel() < nnz:
+        extra = torch.randint(0, total, (int((nnz - keys.numel()) * 1.2) + 16,), generator=g,
+                              device=device)
+        keys = torch.unique(torch.cat([keys, extra]))
+    keys = keys[torch.randperm(keys.numel(), generator=g, device=device)[:nnz]].cpu().numpy()
+    return (keys // N).astype(np.int32), (keys % N).astype(np.int32)
 
 
 RECIPES = {

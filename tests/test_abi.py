@@ -8,6 +8,7 @@ import ctypes as C
 import os
 import re
 import subprocess
+from pathlib import Path
 
 import pytest
 
@@ -61,7 +62,9 @@ def test_status_strings_and_defaults(libpath):
     assert "invalid" in bp.bpmf_strerror(-1)
     cfg = bp.bpmf_config_default(16)
     assert cfg.K == 16 and cfg.nu0 == 16.0 and cfg.path == bp.PATH_MIXED
-    assert cfg.light_max == -1 and cfg.hub_min == -1
+    assert cfg.light_max == -1 and cfg.hub_min == -1 and cfg.tiny_max == -1
+    assert cfg.autotune == 0
+
 
 
 @pytest.mark.parametrize("K", [0, 129])
@@ -95,3 +98,27 @@ def test_product_path_never_imports_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "bpmf_oracle" not in txt, f
+
+
+@pytest.mark.parametrize("pyname,ctype", [("Config", "bpmf_config"), ("Job", "bpmf_job"),
+                                           ("JobResult", "bpmf_job_result")])
+def test_struct_mirrors_match_the_c_layout(tmp_path, pyname, ctype):
+    """The ctypes mirrors have the size and field offsets gcc gives the C structs."""
+    import shutil
+    import paper_1705_04159_gb300 as bp
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    cls = getattr(bp, pyname)
+    names = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({ctype}, {n}));\n' for n in names)
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"bpmf.h\"\n"
+                   f"int main(void) {{\n  printf(\"%zu\\n\", sizeof({ctype}));\n" + body +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    root = Path(__file__).resolve().parents[1]
+    subprocess.run(["gcc", "-I", str(root / "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got[0] == C.sizeof(cls)
+    assert got[1:] == [getattr(cls, n).offset for n in names]
