@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--autotune", type=int, default=1, choices=[0, 1])
+    p.add_argument("--heavy", type=int, default=0, choices=[0, 1, 2],
+                   help="heavy-row kernel: 0 tuned, 1 persistent, 2 one CTA per row")
     p.add_argument("--serving-jobs", type=int, default=256)
     p.add_argument("--serving-iters", type=int, default=50)
     p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],
@@ -199,7 +202,7 @@ def measured_peaks():
 
 # ------------------------------------------------------------- GPU arms --
 
-def device_arm(bp, ds, path, steps, warmup, world, stream):
+def device_arm(bp, ds, path, steps, warmup, world, stream, autotune=1, heavy=0):
     """Steady-state iterations with every input already in HBM."""
     import torch
     dev = torch.device("cuda")
@@ -208,7 +211,8 @@ def device_arm(bp, ds, path, steps, warmup, world, stream):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s = bp.Sampler(ds.M, ds.N, t["train_row"], t["train_col"], t["train_val"], K=ds.K,
-                   alpha=ds.alpha, seed=0, path=path, stream=stream)
+                   alpha=ds.alpha, seed=0, path=path, stream=stream, autotune=autotune,
+                   heavy_kernel=heavy)
     s.set_test(t["test_row"], t["test_col"], t["test_val"])
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
@@ -229,11 +233,12 @@ def device_arm(bp, ds, path, steps, warmup, world, stream):
     phase_ms, phase_cnt, kernels = s.timing()
     rmse = s.test_rmse()
     info = [s.sweep_info(0), s.sweep_info(1)]
+    thresholds = [s.thresholds(0), s.thresholds(1)]
     s.close()
     del t
     torch.cuda.empty_cache()
     return dict(ms=ms, init_s=init_s, phase_ms=phase_ms, phase_cnt=phase_cnt, kernels=kernels,
-                rmse=rmse, info=info)
+                rmse=rmse, info=info, thresholds=thresholds)
 
 
 def serving_arm(bp, n_jobs, iterations, seed=0):
@@ -274,7 +279,7 @@ def serving_arm(bp, n_jobs, iterations, seed=0):
                         "ratings log-U[10k,5M], K in {16,32,64}, mixed path"}
 
 
-def e2e_arm(bp, ds, path, steps, stream):
+def e2e_arm(bp, ds, path, steps, stream, autotune=1):
     """A whole job through the C ABI from pinned host buffers: bpmf_init (H2D of
     the ratings, structure build), bpmf_set_test, `steps` iterations, then the
     factors and the RMSE back to the host."""
@@ -289,7 +294,7 @@ def e2e_arm(bp, ds, path, steps, stream):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     s = bp.Sampler(ds.M, ds.N, host["train_row"], host["train_col"], host["train_val"], K=ds.K,
-                   alpha=ds.alpha, seed=1, path=path, stream=stream)
+                   alpha=ds.alpha, seed=1, path=path, stream=stream, autotune=autotune)
     s.set_test(host["test_row"], host["test_col"], host["test_val"])
     for _ in range(steps):
         s.step()
@@ -381,7 +386,8 @@ def main():
     main_path = {"mixed": bp.PATH_MIXED, "binned": bp.PATH_BINNED, "plain": bp.PATH_PLAIN}[args.path]
 
     with ClockSampler(local) as clk:
-        mixed = device_arm(bp, ds, main_path, args.steps, args.warmup, world, stream)
+        mixed = device_arm(bp, ds, main_path, args.steps, args.warmup, world, stream,
+                           autotune=args.autotune, heavy=args.heavy)
     clocks = clk.summary()
     ms = max_over_ranks(world, mixed["ms"])
     rows = ds.M + ds.N
@@ -398,7 +404,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e = e2e_arm(bp, ds, main_path, args.steps, stream)
+        e = e2e_arm(bp, ds, main_path, args.steps, stream, args.autotune)
         em = max_over_ranks(world, e["ms"])
         e2e = {"value": world * rows * args.steps / (em / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(e["h2d"]), "d2h_bytes_per_step": int(e["d2h"]),
@@ -441,7 +447,10 @@ def main():
             "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
             "init_s": mixed["init_s"], "rmse": {"sample": mixed["rmse"][0], "mean": mixed["rmse"][1]},
             "bins": {"users": mixed["info"][0][0].tolist(), "movies": mixed["info"][1][0].tolist(),
-                     "fp64_rows": [mixed["info"][0][1], mixed["info"][1][1]]},
+                     "fp64_rows": [mixed["info"][0][1], mixed["info"][1][1]],
+                     "thresholds_tiny_light_hub": mixed["thresholds"],
+                     "autotune": "on: timed at the first init (init_s), reused from the "
+                                 "process cache by the e2e job"},
             "plain_fp32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "serving": serving,
         }

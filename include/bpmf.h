@@ -91,8 +91,14 @@ typedef struct {
   int32_t hub_min;    /* rows with degree >= hub_min are split across CTAs; -1: automatic */
   int32_t tiny_max;   /* rows with degree <= tiny_max take the rank-one kernel (BINNED and
                          MIXED paths); -1: automatic */
+  int32_t heavy_kernel; /* heavy rows on the MIXED path: 0 automatic (autotuned, else the
+                           persistent warp-specialised kernel), 1 persistent kernel, 2 one CTA
+                           per row with the Cholesky on tensor cores */
   int32_t autotune;   /* 1: bpmf_init times candidate thresholds for every automatic (-1)
-                         one on this GPU and keeps the fastest; 0: fixed defaults */
+                         one on this GPU and keeps the fastest (paper Sec. IV-B sets its
+                         split threshold by hand); the choice is remembered for the process
+                         per (device, K, path, side shape, degree histogram in powers of
+                         two); 0: fixed defaults */
 } bpmf_config;
 
 /* Fills `cfg` with the defaults: path MIXED, alpha 2, beta0 2, nu0 K,

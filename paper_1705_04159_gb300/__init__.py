@@ -59,7 +59,8 @@ class Config(C.Structure):
         ("K", C.c_int32), ("path", C.c_int32), ("alpha", C.c_double), ("beta0", C.c_double),
         ("nu0", C.c_double), ("mu0", C.c_void_p), ("W0", C.c_void_p), ("seed", C.c_uint64),
         ("order", C.c_int32), ("burnin", C.c_int32), ("light_max", C.c_int32),
-        ("hub_min", C.c_int32), ("tiny_max", C.c_int32), ("autotune", C.c_int32),
+        ("hub_min", C.c_int32), ("tiny_max", C.c_int32), ("heavy_kernel", C.c_int32),
+        ("autotune", C.c_int32),
     ]
 
 
@@ -406,7 +407,7 @@ class Sampler:
 
     def __init__(self, M, N, row, col, val, K, alpha=2.0, beta0=2.0, nu0=None, mu0=None, W0=None,
                  seed=0, path=PATH_MIXED, order=0, burnin=0, light_max=-1, hub_min=-1,
-                 tiny_max=-1, autotune=0, stream=None):
+                 tiny_max=-1, heavy_kernel=0, autotune=0, stream=None):
         cfg = bpmf_config_default(K)
         cfg.alpha = float(alpha)
         cfg.beta0 = float(beta0)
@@ -418,6 +419,7 @@ class Sampler:
         cfg.light_max = int(light_max)
         cfg.hub_min = int(hub_min)
         cfg.tiny_max = int(tiny_max)
+        cfg.heavy_kernel = int(heavy_kernel)
         cfg.autotune = int(autotune)
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.nnz = int(len(row))

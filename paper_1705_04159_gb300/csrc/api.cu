@@ -53,13 +53,15 @@ void free_handle(Handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
-    dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhl);
+    dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhi);
+    dfree(sd.Xlo); dfree(sd.work);
     dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.lchol); dfree(sd.xbar); dfree(sd.S);
     dfree(sd.piece_row); dfree(sd.piece_e0); dfree(sd.piece_e1); dfree(sd.hub_piece0);
   }
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
   dfree(h->flag_rows); dfree(h->flag_count); dfree(h->trow); dfree(h->tcol); dfree(h->tval);
   dfree(h->tsum); dfree(h->terr); dfree(h->hub_part); dfree(h->d_iter); dfree(h->d_navg);
+  dfree(h->ws_counter);
   delete h;
 }
 
@@ -245,6 +247,7 @@ void bpmf_config_default(bpmf_config* c, int32_t K) {
   c->light_max = -1;
   c->hub_min = -1;
   c->tiny_max = -1;
+  c->heavy_kernel = 0;
   c->autotune = 0;
 }
 
@@ -277,7 +280,8 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
   if (K < 1 || K > kMaxK || M < 1 || N < 1 || M >= (1LL << 31) || N >= (1LL << 31) || nnz < 0 ||
       nnz >= (1LL << 31) || (nnz > 0 && (!row || !col || !val)) || !(cfg->alpha > 0.0) ||
       !(cfg->beta0 > 0.0) || !(cfg->nu0 > (double)K - 1.0) || cfg->path < BPMF_PATH_PLAIN ||
-      cfg->path > BPMF_PATH_MIXED || (cfg->order != 0 && cfg->order != 1) || cfg->burnin < 0) {
+      cfg->path > BPMF_PATH_MIXED || (cfg->order != 0 && cfg->order != 1) || cfg->burnin < 0 ||
+      cfg->heavy_kernel < 0 || cfg->heavy_kernel > 2) {
     set_error("bpmf_init: invalid shape or configuration (K=%d M=%lld N=%lld nnz=%lld)", K,
               (long long)M, (long long)N, (long long)nnz);
     return BPMF_EINVAL;
@@ -318,6 +322,11 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       if ((rc = dalloc(&sd.mu, K))) break;
       if ((rc = dalloc(&sd.lamaug, (int64_t)(K + 1) * (K + 1)))) break;
       if ((rc = dalloc(&sd.lchol, KK))) break;
+      if (cfg->path == BPMF_PATH_MIXED) {
+        sd.KS = (K + 7) & ~7;
+        if ((rc = dalloc(&sd.Xhi, sd.R * sd.KS))) break;
+        if ((rc = dalloc(&sd.Xlo, sd.R * sd.KS))) break;
+      }
       if ((rc = dalloc(&sd.xbar, K))) break;
       if ((rc = dalloc(&sd.S, KK))) break;
     }
@@ -334,6 +343,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     if ((rc = dalloc(&h->terr, 2))) break;
     if ((rc = dalloc(&h->d_iter, 1))) break;
     if ((rc = dalloc(&h->d_navg, 1))) break;
+    if ((rc = dalloc(&h->ws_counter, 1))) break;
     if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_iter, 0, sizeof(uint32_t), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_navg, 0, sizeof(int64_t), h->stream) != cudaSuccess) {
@@ -379,6 +389,8 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     if ((rc = setup_bins(h, BPMF_MOVIES))) break;
     if ((rc = launch_init_factors(h, BPMF_USERS))) break;
     if ((rc = launch_init_factors(h, BPMF_MOVIES))) break;
+    if ((rc = launch_refresh_shadow(h, BPMF_USERS))) break;
+    if ((rc = launch_refresh_shadow(h, BPMF_MOVIES))) break;
     if (cfg->autotune) {
       float* scratch = nullptr;
       if ((rc = dalloc(&scratch, std::max(M, N) * K))) break;
@@ -574,6 +586,8 @@ int bpmf_set_state(bpmf_t* hh, const float* U, const float* V, const double* hyp
   const int64_t KK = (int64_t)K * K;
   if (U) BPMF_CUDA_CHECK(cudaMemcpyAsync(h->side[0].X, U, sizeof(float) * h->M * K, kind, h->stream));
   if (V) BPMF_CUDA_CHECK(cudaMemcpyAsync(h->side[1].X, V, sizeof(float) * h->N * K, kind, h->stream));
+  if (U) BPMF_TRY(launch_refresh_shadow(h, 0));
+  if (V) BPMF_TRY(launch_refresh_shadow(h, 1));
   if (hyper) {
     for (int s = 0; s < 2; ++s) {
       const double* base = hyper + s * (KK + K);

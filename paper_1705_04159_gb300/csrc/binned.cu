@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "bpmf_impl.cuh"
@@ -46,10 +48,15 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
     BPMF_TRY(launch_hub_finish_fp32(f, st, &h->kernels));
   }
   SweepArgs r = a;
-  if (tc) {
+  if (tc || (h->cfg.path == BPMF_PATH_MIXED && ws_supported(h->K))) {
     r.row_begin = e_hub;
     r.row_end = e_heavy;
-    BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
+    if (sd.Xhi && ws_supported(h->K) && !sd.heavy_tc)
+      BPMF_TRY(launch_rows_ws(r, h->num_sms, h->ws_counter, h->status, st, &h->kernels));
+    else if (tc)
+      BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
+    else
+      BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
     r.row_begin = e_heavy;
     r.row_end = e_light;
     BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
@@ -164,11 +171,20 @@ int setup_bins(Handle* h, int s) {
   BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.perm_h.data(), sd.perm, sizeof(int32_t) * R,
                                   cudaMemcpyDeviceToHost, st));
   BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
+  std::vector<int4> work(R > 0 ? R : 1);
   for (int64_t q = 0; q < R; ++q) {
     const int32_t r = sd.perm_h[q];
     sd.deg_h[q] = sd.ptr_h[r + 1] - sd.ptr_h[r];
+    work[q] = make_int4(r, (int)sd.ptr_h[r], (int)sd.ptr_h[r + 1], 0);
   }
+  cudaFree(sd.work);
+  sd.work = nullptr;
+  BPMF_CUDA_CHECK(cudaMalloc(&sd.work, sizeof(int4) * work.size()));
+  BPMF_CUDA_CHECK(cudaMemcpyAsync(sd.work, work.data(), sizeof(int4) * work.size(),
+                                  cudaMemcpyHostToDevice, st));
+  BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
   sd.hub_min = 0;  // forces the pieces to be built
+  sd.heavy_tc = h->cfg.heavy_kernel == 2 && tc_supported(h->K);
   const int64_t tiny = h->cfg.tiny_max >= 0 ? h->cfg.tiny_max : default_tiny_max(h);
   const int64_t light = h->cfg.light_max >= 0 ? h->cfg.light_max : tiny;
   const int64_t hub = h->cfg.hub_min >= 0 ? h->cfg.hub_min : 2 * kPiece;
@@ -229,14 +245,60 @@ std::vector<int64_t> distinct_cuts(const SideDev& sd, std::vector<int64_t> c) {
   return out;
 }
 
+// Tuned thresholds per (device, K, path, configured thresholds, side shape,
+// degree histogram in powers of two), shared by the samplers of a process: a
+// second job of the same shape reuses the first one's timings.
+struct TuneKey {
+  std::vector<int64_t> v;
+  bool operator<(const TuneKey& o) const { return v < o.v; }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::vector<int64_t>> g_tuned;
+
+TuneKey tune_key(const Handle* h, int s) {
+  const SideDev& sd = h->side[s];
+  TuneKey k;
+  k.v = {h->device, h->K, h->cfg.path, h->cfg.tiny_max, h->cfg.light_max, h->cfg.hub_min,
+         h->cfg.heavy_kernel, s, sd.R};
+  std::vector<int64_t> hist(40, 0);
+  int64_t nnz = 0;
+  for (int64_t d : sd.deg_h) {
+    int b = 0;
+    while ((int64_t)1 << b <= d) ++b;
+    hist[b] += 1;
+    nnz += d;
+  }
+  k.v.push_back(nnz);
+  k.v.insert(k.v.end(), hist.begin(), hist.end());
+  return k;
+}
+
 }  // namespace
 
 int autotune_bins(Handle* h, int s, float* scratch) {
   SideDev& sd = h->side[s];
   if (h->cfg.path == BPMF_PATH_PLAIN || sd.R == 0) return BPMF_OK;
+  const TuneKey key = tune_key(h, s);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      sd.heavy_tc = it->second[3] != 0;
+      return apply_bins(h, s, it->second[0], it->second[1], it->second[2]);
+    }
+  }
   BPMF_TRY(launch_hyper(h, s));
   const int reps = 2;
   float ms = 0.f;
+  if (h->cfg.heavy_kernel == 0 && h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K) &&
+      ws_supported(h->K) && sd.Xhi) {
+    float t_ws = 0.f, t_tc = 0.f;
+    sd.heavy_tc = false;
+    BPMF_TRY(time_sweep(h, s, scratch, reps, &t_ws));
+    sd.heavy_tc = true;
+    BPMF_TRY(time_sweep(h, s, scratch, reps, &t_tc));
+    sd.heavy_tc = t_tc < t_ws;
+  }
   const int64_t maxdeg = sd.deg_h.empty() ? 0 : sd.deg_h[0];
   if (h->cfg.hub_min < 0 && maxdeg >= 2048) {
     int64_t best_v = sd.hub_min;
@@ -286,6 +348,8 @@ int autotune_bins(Handle* h, int s, float* scratch) {
   // without them, as before tuning
   sd.have_hyper = false;
   sd.have_stats = false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = {sd.tiny_max, sd.light_max, sd.hub_min, sd.heavy_tc ? 1 : 0};
   return BPMF_OK;
 }
 

@@ -8,6 +8,7 @@
 //   Lambda f32 K*K, b0 = Lambda mu f32 K), hyper statistics f64.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,8 +43,11 @@ struct SideDev {
   int32_t* idx = nullptr;
   float* val = nullptr;
   int32_t* perm = nullptr;
+  int4* work = nullptr;     // [R] per slot of the degree order: (row, ptr[row], ptr[row+1], 0)
   float* X = nullptr;      // R*K
-  uint32_t* Xhl = nullptr; // R*K packed (bf16 hi | bf16 lo << 16), mixed path only
+  __nv_bfloat16* Xhi = nullptr;  // R*KS bf16 hi of X (mixed path): x ~= hi + lo to ~2^-16
+  __nv_bfloat16* Xlo = nullptr;  // R*KS bf16 lo
+  int KS = 0;                    // shadow row stride: K rounded up to 8
   double* lam = nullptr;   // K*K
   double* mu = nullptr;    // K
   float* lamaug = nullptr; // (K+1)^2: Lambda_s bordered by b0 = Lambda_s mu_s (row and column K)
@@ -62,6 +66,7 @@ struct SideDev {
   std::vector<int64_t> ptr_h;   // host: row pointers
   std::vector<int32_t> perm_h;  // host: degree order
   int64_t max_deg = 0;
+  bool heavy_tc = false;  // heavy bin on the per-row tensor-core kernel instead of the persistent one
   bool have_hyper = false;
   bool have_stats = false;
   int64_t fp64_rows = 0;
@@ -108,6 +113,7 @@ struct Handle {
   bool graph_timing = false;          // timing state the graph was captured with
   int64_t graph_kernels = 0;          // kernels per replay
 
+  int* ws_counter = nullptr;  // row counter of the persistent row kernel
   // hub split partial Grams
   float* hub_part = nullptr;
   int64_t hub_part_len = 0;

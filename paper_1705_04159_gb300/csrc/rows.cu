@@ -365,6 +365,10 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.piece_e1 = sd.piece_e1;
   a.hub_piece0 = sd.hub_piece0;
   a.part = h->hub_part;
+  a.work = sd.work;
+  a.Vhi = od.Xhi;
+  a.Vlo = od.Xlo;
+  a.KS = od.KS;
   return a;
 }
 
@@ -394,7 +398,8 @@ int launch_sweep(Handle* h, int s) {
     BPMF_TRY(launch_fp64_redo(h, s, a));
     h->kernels += 1;
   }
-  return BPMF_OK;
+  // the next half-sweep gathers this side's new rows from the shadow
+  return launch_refresh_shadow(h, s);
 }
 
 int launch_init_factors(Handle* h, int s) {

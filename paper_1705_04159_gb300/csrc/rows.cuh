@@ -1,6 +1,8 @@
 // rows.cuh -- arguments shared by the row-update kernels of one half-sweep.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "bpmf_impl.cuh"
 
 namespace gb {
@@ -31,6 +33,12 @@ struct SweepArgs {
   const int64_t* piece_e1;
   const int32_t* hub_piece0;
   float* part;          // partial Gram tiles [piece][tile][TM * TM]
+  // bf16 hi/lo shadow of the other side's factors, rows padded to KS (mixed path)
+  const __nv_bfloat16* Vhi;
+  const __nv_bfloat16* Vlo;
+  int KS;
+  // per slot of the degree order: (row, first rating, one past the last, 0)
+  const int4* work;
 };
 
 SweepArgs make_sweep_args(Handle* h, int s);
@@ -47,6 +55,10 @@ int launch_rows_tc(const SweepArgs& a, int* status, cudaStream_t st, int64_t* la
 int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStream_t st,
                      int64_t* launches);
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
+// heavy rows by the persistent warp-specialised kernel (rows_ws.cu)
+bool ws_supported(int K);
+int launch_rows_ws(const SweepArgs& a, int num_sms, int* counter, int* status, cudaStream_t st,
+                   int64_t* launches);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
 int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
 

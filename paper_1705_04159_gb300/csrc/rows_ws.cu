@@ -1,0 +1,763 @@
+// rows_ws.cu -- row draws by a persistent, warp-specialised kernel (mixed
+// path, heavy rows).
+//
+// Same conditional as rows.cu and rows_tc.cu (Algorithm 1's row update): the
+// Gram of the rating-augmented neighbour vectors x_j = [v_j, r_ij] gives
+// Lambda* = Lambda_s + alpha sum v_j v_j^T and b = Lambda_s mu_s + alpha sum
+// r_ij v_j as one bordered matrix; its Cholesky factor L holds y = L^-1 b in
+// its last row; u = L^-T (y + z).
+//
+// One CTA per SM takes rows of the degree order from a global counter
+// (largest first) and runs them through a pipeline of warp roles:
+//   gather (warps 0-3): copies the bf16 hi/lo shadow rows of the neighbours,
+//     16 per stage, with 16-byte cp.async straight into MN-major operand
+//     tiles (feature-contiguous 8 x 16-byte core matrices: chunk c of
+//     neighbour k at c * 256 + (k / 8) * 128 + (k % 8) * 16), plus the
+//     chunk holding the rating feature, into a ring of stages;
+//   MMA (warp 8, one thread): per stage hi.hi + hi.lo + lo.hi into one of two
+//     FP32 accumulators in tensor memory (G = X^T X with X the stage's
+//     neighbours x features; lo.lo, ~2^-16 relative, is dropped);
+//   drain (warps 4-7, thread m = tensor-memory lane m = matrix row m):
+//     forms A = base + alpha G (base = bordered [[Lambda_s, b0], [b0^T, 0]])
+//     and writes its lower triangle as 8 x 8 FP32 tiles into a free
+//     consumer slot, releasing the accumulator for the next row;
+//   consumers (warps 9.., one row each): blocked right-looking Cholesky of
+//     the slot (per 8-column panel: the diagonal tile by shuffles, the panel
+//     by forward substitution, the trailing tiles as register-blocked
+//     8 x 8 x 8 updates), then u = L^-T (y + z) by back substitution.
+// So the tensor cores, the gathers and the FP32 factorisations of up to
+// seven rows per SM overlap, with no CTA-wide barrier on the way.
+//
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// kStatusTimeout, every role leaves its loop, outstanding copies and MMAs
+// are waited for (bounded) and the tensor memory is freed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bpmf_impl.cuh"
+#include "rows.cuh"
+#include "tc_ptx.cuh"
+#include "tile_chol.cuh"
+
+namespace gb {
+namespace {
+
+constexpr int kWsNb = 16;            // neighbours per stage (one MMA K-step)
+constexpr int kWsLBO = 128;          // operand tiles: bytes between the two 8-neighbour groups
+constexpr int kWsSBO = 256;          //   and between 8-feature chunks
+constexpr int kWsOpBytes = 16 * kWsSBO;        // 128 features (the MMA reads M = 128 rows)
+constexpr int kWsStageBytes = 2 * kWsOpBytes;  // hi + lo
+constexpr int kWsMaxStages = 8;
+constexpr int kWsMaxCons = 7;
+constexpr int kWsRecs = 16;          // row records in flight: > stages + 2 (see the gather loop)
+constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (4 floats of skew against bank conflicts)
+constexpr int kWsGather = 128, kWsDrain = 128;
+constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
+constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound per wait
+constexpr uint32_t kWsAccCols = 128;
+
+struct WsGeom {
+  int K, KA, g, KP, NP, nfull, cb, ntile;
+  __host__ __device__ explicit WsGeom(int K_) : K(K_) {
+    KA = K + 1;
+    g = (KA + 7) / 8;
+    KP = 8 * g;
+    NP = (KA + 15) & ~15;
+    nfull = K / 8;
+    cb = K / 8;
+    ntile = g * (g + 1) / 2;
+  }
+  // consumer slot: header (4 ints), tiles, diag0, rinv, z
+  __host__ __device__ int slot_floats() const { return 4 + ntile * kWsTileF + 3 * KP; }
+};
+
+struct StageMeta {
+  int rec;    // row record index
+  int cnt;    // neighbours in this stage (0 for a row without ratings)
+  int flags;  // 1: first stage of the row, 2: last stage of the row
+  int pad;
+};
+struct RowRec {
+  int row;  // -1: no more rows
+  int nst;  // stages with ratings (0: the row has none)
+  int pad0, pad1;
+};
+
+struct WsShared {
+  uint8_t* stages;
+  float* base;   // bordered [[Lambda_s, b0], [b0^T, 0]] as lower 8 x 8 tiles, identity padding
+  float* slots;
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* acc_full;
+  uint64_t* acc_empty;
+  uint64_t* slot_full;
+  uint64_t* slot_empty;
+  uint64_t* fin;
+  uint64_t* row_ready;  // the gather leader published the next row
+  uint64_t* row_read;   // every gather thread has read it
+  StageMeta* meta;
+  RowRec* recs;
+  float* rating;   // [stage][neighbour]: ratings waiting to be patched in
+  int* next_row;   // [4]: row, first rating, last rating
+  int* abort;
+  uint32_t* taddr;
+};
+
+__host__ __device__ inline int ws_fixed_bytes() {
+  // barriers (2 S + 4 + 2 C + 3), stage meta, row records, ratings, next_row, abort, taddr
+  return 8 * (2 * kWsMaxStages + 4 + 2 * kWsMaxCons + 3) + 16 * kWsMaxStages + 16 * kWsRecs +
+         4 * kWsMaxStages * kWsNb + 32;
+}
+// stages, base tiles, consumer slots, then the fixed part
+__host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C) {
+  return S * kWsStageBytes + G.ntile * kWsTileF * 4 + C * G.slot_floats() * 4 + ws_fixed_bytes();
+}
+
+__device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C) {
+  WsShared w;
+  w.stages = base;
+  w.base = reinterpret_cast<float*>(base + S * kWsStageBytes);
+  w.slots = w.base + G.ntile * kWsTileF;
+  uint8_t* p = reinterpret_cast<uint8_t*>(w.slots + C * G.slot_floats());
+  uint64_t* b = reinterpret_cast<uint64_t*>(p);
+  w.full = b;
+  w.empty = b + kWsMaxStages;
+  w.acc_full = b + 2 * kWsMaxStages;
+  w.acc_empty = w.acc_full + 2;
+  w.slot_full = w.acc_empty + 2;
+  w.slot_empty = w.slot_full + kWsMaxCons;
+  w.fin = w.slot_empty + kWsMaxCons;
+  w.row_ready = w.fin + 1;
+  w.row_read = w.fin + 2;
+  p = reinterpret_cast<uint8_t*>(w.fin + 3);
+  w.meta = reinterpret_cast<StageMeta*>(p);
+  w.recs = reinterpret_cast<RowRec*>(p + 16 * kWsMaxStages);
+  w.rating = reinterpret_cast<float*>(p + 16 * kWsMaxStages + 16 * kWsRecs);
+  int* q = reinterpret_cast<int*>(w.rating + kWsMaxStages * kWsNb);
+  w.next_row = q;
+  w.abort = q + 4;
+  w.taddr = reinterpret_cast<uint32_t*>(q + 5);
+  return w;
+}
+
+// Bounded wait by one thread: gives up (setting abort) after kWsPolls
+// suspending polls, or as soon as another role has aborted.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kWsPolls; ++i) {
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+// The same by a whole warp: every lane waits (and so acquires what the
+// barrier publishes); the outcome is made uniform across the warp, so no
+// lane leaves a loop that its neighbours stay in.
+__device__ __forceinline__ bool ws_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const bool ok = ws_wait(bar, parity, abort);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// wait until at most `n` (0..6) groups of this thread are pending
+__device__ __forceinline__ void cp_async_wait_dyn(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    default: cp_async_wait<6>(); break;
+  }
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// kind::f16 instruction descriptor, BF16 operands both MN-major (bits 15, 16).
+__device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
+
+// ------------------------------------------------------------- gather --
+// Stage s receives neighbours [e, e + cnt) (cnt <= 16).  Thread t of the
+// gather group handles neighbour k = t % 16 and chunks c = t / 16 + 8 i, so
+// that 16 consecutive threads write 256 contiguous bytes.  Chunks 0 ..
+// ceil(K/8) - 1 are 16-byte copies of the shadow row (its padding past K is
+// zero); the rating (feature K, in chunk cb = K / 8) is patched in once the
+// copy of its chunk has landed (ws_patch_rating).  Rows k >= cnt are zeroed.
+__device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs& a,
+                                                uint8_t* stage, int cnt, int32_t j) {
+  const int t = threadIdx.x;  // 0 .. 127
+  const int k = t & 15;
+  const bool live = k < cnt;
+  const __nv_bfloat16* hrow = a.Vhi + (int64_t)j * a.KS;
+  const __nv_bfloat16* lrow = a.Vlo + (int64_t)j * a.KS;
+  const uint32_t hi = smem_u32(stage), lo = hi + kWsOpBytes;
+  const int koff = (k >> 3) * kWsLBO + (k & 7) * 16;
+  const int ncopy = (G.K + 7) >> 3;
+  for (int c = t >> 4; c <= G.cb; c += 8) {
+    const int off = c * kWsSBO + koff;
+    if (live && c < ncopy) {
+      cp_async16(hi + off, hrow + 8 * c);
+      cp_async16(lo + off, lrow + 8 * c);
+    } else {
+      *reinterpret_cast<uint4*>(stage + off) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(stage + kWsOpBytes + off) = make_uint4(0, 0, 0, 0);
+    }
+  }
+}
+
+// Feature K of neighbour k = the rating r, as bf16 hi and lo, written by the
+// thread that copied chunk cb of that neighbour after its copy completed.
+__device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r) {
+  const int t = threadIdx.x;
+  if ((t >> 4) != (G.cb & 7)) return;
+  const int k = t & 15;
+  const int off = G.cb * kWsSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
+  const __nv_bfloat16 h = __float2bfloat16_rn(r);
+  *reinterpret_cast<__nv_bfloat16*>(stage + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(stage + kWsOpBytes + off) =
+      __float2bfloat16_rn(r - __bfloat162float(h));
+}
+
+__device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
+                                          int S, int* counter) {
+  const int t = threadIdx.x;
+  const int k = t & 15;
+  const bool patcher = (t >> 4) == (G.cb & 7);
+  const int nrows = (int)(a.row_end - a.row_begin);
+  uint32_t n = 0;          // stage sequence number
+  int q = 0;               // row sequence number
+  // copies of up to S - 1 stages are in flight; stage n is signalled full
+  // once stage n + S - 2 has been issued (the ring keeps one stage spare,
+  // so the gather never waits for a stage it has not yet signalled)
+  const int lag = S - 2;
+  uint32_t signalled = 0;  // stages [0, signalled) have been signalled
+  // thread 0 prefetches the next row's work entry (row, first, last rating)
+  int4 wk = make_int4(-1, 0, 0, 0);
+  int next_slot = 0;
+  if (t == 0) {
+    next_slot = atomicAdd(counter, 1);
+    if (next_slot < nrows) wk = __ldg(a.work + a.row_begin + next_slot);
+  }
+  for (;;) {
+    if (t == 0) {
+      // the slot is free once every gather thread has read the previous row
+      const bool ok = q == 0 || ws_wait(w.row_read, (uint32_t)(q - 1) & 1u, w.abort);
+      w.next_row[0] = ok ? wk.x : -1;
+      w.next_row[1] = wk.y;
+      w.next_row[2] = wk.z;
+      mbar_arrive(w.row_ready);
+      if (ok && wk.x >= 0) next_slot = atomicAdd(counter, 1);  // used after the first stage
+    }
+    if (!ws_wait_warp(w.row_ready, (uint32_t)q & 1u, w.abort)) break;
+    const int row = w.next_row[0];
+    const int e0 = w.next_row[1], e1 = row >= 0 ? w.next_row[2] : e0;
+    mbar_arrive(w.row_read);
+    const int nst_r = (e1 - e0 + kWsNb - 1) / kWsNb;
+    const int nst = nst_r > 0 ? nst_r : 1;
+    // neighbour id and rating of this thread for the current stage, loaded a
+    // stage ahead
+    int32_t jc = 0;
+    float rc = 0.f;
+    if (row >= 0 && k < e1 - e0) {
+      jc = __ldg(a.idx + e0 + k);
+      rc = __ldg(a.val + e0 + k);
+    }
+    bool stop = false;
+    for (int st = 0; st < nst; ++st) {
+      const int s = (int)(n % (uint32_t)S);
+      const int e = e0 + st * kWsNb;
+      const int cnt = row < 0 ? 0 : (e1 - e < kWsNb ? (e1 - e > 0 ? e1 - e : 0) : kWsNb);
+      int32_t jn = 0;
+      float rn = 0.f;
+      if (st + 1 < nst && k < e1 - e - kWsNb) {
+        jn = __ldg(a.idx + e + kWsNb + k);
+        rn = __ldg(a.val + e + kWsNb + k);
+      }
+      if (t == 0 && st == 0 && next_slot < nrows && row >= 0)
+        wk = __ldg(a.work + a.row_begin + next_slot);
+      else if (t == 0 && st == 0)
+        wk = make_int4(-1, 0, 0, 0);
+      if (!ws_wait_warp(&w.empty[s], ((n / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
+        stop = true;
+        break;
+      }
+      if (t == 0) {
+        if (st == 0) {
+          w.recs[q % kWsRecs].row = row;
+          w.recs[q % kWsRecs].nst = row < 0 ? 0 : nst_r;
+        }
+        w.meta[s].rec = q % kWsRecs;
+        w.meta[s].cnt = cnt;
+        w.meta[s].flags = (st == 0 ? 1 : 0) | (st == nst - 1 ? 2 : 0);
+      }
+      if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, jc);
+      if (patcher) w.rating[s * kWsNb + k] = k < cnt ? rc : 0.f;
+      cp_async_commit();
+      ++n;
+      if (n - signalled > (uint32_t)lag) {
+        cp_async_wait_dyn(lag);
+        const int ss = (int)(signalled % (uint32_t)S);
+        ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + k]);
+        fence_proxy_async_smem();
+        mbar_arrive(&w.full[ss]);
+        ++signalled;
+      }
+      jc = jn;
+      rc = rn;
+    }
+    if (stop || row < 0) break;
+    ++q;
+  }
+  cp_async_wait<0>();
+  for (; signalled < n; ++signalled) {
+    const int ss = (int)(signalled % (uint32_t)S);
+    ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + k]);
+    fence_proxy_async_smem();
+    mbar_arrive(&w.full[ss]);
+  }
+}
+
+// ---------------------------------------------------------------- MMA --
+__device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S, uint32_t tmem) {
+  const uint32_t idesc = idesc_bf16_mn(128, G.NP);
+  const uint32_t base = smem_u32(w.stages);
+  uint32_t n = 0;
+  int q = 0;
+  for (;;) {
+    const int s = (int)(n % (uint32_t)S);
+    if (!ws_wait(&w.full[s], (n / (uint32_t)S) & 1u, w.abort)) break;
+    tc_fence_after();
+    const StageMeta m = w.meta[s];
+    const RowRec r = w.recs[m.rec];
+    const int b = q & 1;
+    if (m.flags & 1) {
+      if (!ws_wait(&w.acc_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, w.abort)) break;
+      tc_fence_after();
+    }
+    const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
+    if (m.cnt > 0) {
+      const uint32_t hi = base + (uint32_t)s * kWsStageBytes, lo = hi + kWsOpBytes;
+      const uint64_t dh = smem_desc_kmajor(hi, kWsLBO, kWsSBO);
+      const uint64_t dl = smem_desc_kmajor(lo, kWsLBO, kWsSBO);
+      tc_mma_bf16(acc, dh, dh, idesc, (m.flags & 1) ? 0u : 1u);
+      tc_mma_bf16(acc, dh, dl, idesc, 1u);
+      tc_mma_bf16(acc, dl, dh, idesc, 1u);
+    }
+    tc_commit(&w.empty[s]);
+    ++n;
+    if (m.flags & 2) {
+      tc_commit(&w.acc_full[b]);
+      ++q;
+      if (r.row < 0) break;
+    }
+  }
+  // every MMA issued has completed before the tensor memory is freed
+  tc_commit(w.fin);
+  uint32_t polls = 0;
+  while (!mbar_try_wait_sleep(w.fin, 0, 20000u) && ++polls < kWsPolls) {
+  }
+}
+
+__device__ __forceinline__ void ld8(const float* p, float (&x)[8]) {
+  const float4 u = reinterpret_cast<const float4*>(p)[0];
+  const float4 v = reinterpret_cast<const float4*>(p)[1];
+  x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+  x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+}
+__device__ __forceinline__ void st8(float* p, const float (&x)[8]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(x[0], x[1], x[2], x[3]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+
+// Base tiles: row m of tile (m / 8, J) for J <= m / 8, written once per launch
+// by the drain threads from the FP32 bordered hyper matrix.
+__device__ __forceinline__ void ws_fill_base(const SweepArgs& a, const WsGeom& G, float* base) {
+  for (int m = threadIdx.x - kWsGather; m < G.KP; m += kWsDrain) {
+    const int I = m >> 3, p = m & 7;
+    for (int J = 0; J <= I; ++J) {
+      float x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int n = 8 * J + i;
+        x[i] = (m < G.KA && n < G.KA) ? (n <= m ? __ldg(a.lamaug + m * G.KA + n) : 0.f)
+                                      : (n == m ? 1.f : 0.f);
+      }
+      st8(base + (I * (I + 1) / 2 + J) * kWsTileF + p * 8, x);
+    }
+  }
+}
+
+// -------------------------------------------------------------- drain --
+// Thread m (0..127) owns tensor-memory lane m = row m of the accumulator.
+__device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, const WsShared& w, int C,
+                         uint32_t tmem) {
+  const int m = threadIdx.x - kWsGather;
+  const int wq = m >> 5;  // warp quarter: lanes 32 wq .. 32 wq + 31
+  const int I = m >> 3, p = m & 7;
+  const int slotf = G.slot_floats();
+  int q = 0;
+  for (;;) {
+    const int b = q & 1;
+    if (!ws_wait_warp(&w.acc_full[b], (uint32_t)(q >> 1) & 1u, w.abort)) return;
+    tc_fence_after();
+    const RowRec r = w.recs[q % kWsRecs];
+    if (r.row < 0) {
+      // one stop record per consumer, in slot order
+      for (int i = 0; i < C; ++i) {
+        const int c = (q + i) % C;
+        const int use = (q + i) / C;
+        if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)use & 1u) ^ 1u, w.abort)) return;
+        if (m == 0) reinterpret_cast<int*>(w.slots + c * slotf)[0] = -1;
+        mbar_arrive(&w.slot_full[c]);
+      }
+      return;
+    }
+    const int c = q % C;
+    if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)(q / C) & 1u) ^ 1u, w.abort)) return;
+    float* slot = w.slots + c * slotf;
+    float* tiles = slot + 4;
+    float* diag0 = tiles + G.ntile * kWsTileF;
+    const uint32_t lane_base = tmem + (uint32_t)b * kWsAccCols + ((uint32_t)(32 * wq) << 16);
+    const bool gram = r.nst > 0;
+    // columns 0 .. 32 wq + 31 cover the lower triangle of this warp's rows
+    const int ncol = 32 * wq + 32 < G.NP ? 32 * wq + 32 : G.NP;
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
+      float v[16];
+      if (gram) {
+        tmem_ld16(lane_base + (uint32_t)c0, v);
+        tmem_wait_ld();
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (m < G.KP) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int J = (c0 >> 3) + h;
+          if (J <= I) {
+            float x[8];
+            float dv = 0.f;
+            const int toff = (I * (I + 1) / 2 + J) * kWsTileF + p * 8;
+            ld8(w.base + toff, x);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int n = 8 * J + i;
+              if (m < G.KA && n <= m) x[i] = fmaf(a.alpha, v[8 * h + i], x[i]);
+              if (n == m) dv = x[i];
+            }
+            float* dst = tiles + toff;
+            reinterpret_cast<float4*>(dst)[0] = make_float4(x[0], x[1], x[2], x[3]);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(x[4], x[5], x[6], x[7]);
+            if (J == I && m < G.K) diag0[m] = dv;
+          }
+        }
+      }
+    }
+    if (m == 0) reinterpret_cast<int*>(slot)[0] = r.row;
+    tc_fence_before();
+    mbar_arrive(&w.acc_empty[b]);
+    mbar_arrive(&w.slot_full[c]);
+    ++q;
+  }
+}
+
+// ----------------------------------------------------------- consumer --
+__device__ __forceinline__ int tidx(int I, int J) { return I * (I + 1) / 2 + J; }
+
+// Blocked right-looking Cholesky of the slot's tiles by one warp.  Returns
+// false if a pivot (of rows 0..K-1) fell below kPivotRel of its starting
+// diagonal; row K (the bordered right-hand side) and the padding rows are
+// never tested.
+__device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const float* diag0, float* rinv, int lane) {
+  bool fail = false;
+  for (int p = 0; p < G.g; ++p) {
+    // (a) diagonal tile: lane r < 8 holds row r
+    float* D = T + tidx(p, p) * kWsTileF;
+    float r[8];
+    ld8(D + (lane & 7) * 8, r);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int idx = 8 * p + c;
+      float piv = __shfl_sync(0xffffffffu, r[c], c);
+      if (idx < G.K) {
+        const float d0 = diag0[idx];
+        if (!(piv > kPivotRel * d0)) {
+          fail = true;
+          piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+        }
+      } else {
+        piv = fmaxf(piv, FLT_MIN);  // row K (never used as a pivot) or padding (1)
+      }
+      const float rd = rsqrtf(piv);
+      if (lane == c) {
+        r[c] = piv * rd;
+        rinv[idx] = rd;
+      } else if (lane > c) {
+        r[c] *= rd;
+      }
+#pragma unroll
+      for (int s2 = c + 1; s2 < 8; ++s2) {
+        const float ls = __shfl_sync(0xffffffffu, r[c], s2);
+        if (lane >= s2) r[s2] = fmaf(-r[c], ls, r[s2]);
+      }
+    }
+    if (lane < 8) st8(D + lane * 8, r);
+    __syncwarp();
+    // (b) panel rows below: x L_pp^T = a, row by row
+    const int nb = G.g - 1 - p;
+    for (int rr = lane; rr < 8 * nb; rr += 32) {
+      const int I = p + 1 + (rr >> 3);
+      float* row = T + tidx(I, p) * kWsTileF + (rr & 7) * 8;
+      float x[8];
+      ld8(row, x);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float dr[8];
+        ld8(D + c * 8, dr);
+        float t = x[c];
+#pragma unroll
+        for (int s2 = 0; s2 < c; ++s2) t = fmaf(-x[s2], dr[s2], t);
+        x[c] = t * rinv[8 * p + c];
+      }
+      st8(row, x);
+    }
+    __syncwarp();
+    // (c) trailing tiles (I, J), p < J <= I: A_IJ -= L_Ip L_Jp^T
+    const int ntl = nb * (nb + 1) / 2;
+    for (int tt = lane; tt < ntl; tt += 32) {
+      int i0 = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
+      while ((i0 + 1) * (i0 + 2) / 2 <= tt) ++i0;
+      while (i0 * (i0 + 1) / 2 > tt) --i0;
+      const int I = p + 1 + i0, J = p + 1 + (tt - i0 * (i0 + 1) / 2);
+      const float* LI = T + tidx(I, p) * kWsTileF;
+      const float* LJ = T + tidx(J, p) * kWsTileF;
+      float* A = T + tidx(I, J) * kWsTileF;
+      float lj[8][8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) ld8(LJ + jj * 8, lj[jj]);
+#pragma unroll
+      for (int ii = 0; ii < 8; ++ii) {
+        float li[8], ar[8];
+        ld8(LI + ii * 8, li);
+        ld8(A + ii * 8, ar);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          float s3 = ar[jj];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) s3 = fmaf(-li[kk], lj[jj][kk], s3);
+          ar[jj] = s3;
+        }
+        st8(A + ii * 8, ar);
+      }
+    }
+    __syncwarp();
+  }
+  return !fail;
+}
+
+__device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, const WsShared& w, int C) {
+  const int c = (threadIdx.x >> 5) - kWsConsWarp0;
+  const int lane = threadIdx.x & 31;
+  float* slot = w.slots + c * G.slot_floats();
+  float* T = slot + 4;
+  float* diag0 = T + G.ntile * kWsTileF;
+  float* rinv = diag0 + G.KP;
+  float* zv = rinv + G.KP;
+  const uint32_t tw = *a.tp;
+  const int K = G.K;
+  for (int qc = 0;; ++qc) {
+    if (!ws_wait_warp(&w.slot_full[c], (uint32_t)qc & 1u, w.abort)) return;
+    const int row = reinterpret_cast<const int*>(slot)[0];
+    if (row < 0) return;
+    for (int qd = lane; 4 * qd < K; qd += 32) {
+      const float4 z = normal4_f32(philox(make_uint4((uint32_t)row, tw, (uint32_t)qd, a.sw), a.key));
+      zv[4 * qd] = z.x;
+      if (4 * qd + 1 < K) zv[4 * qd + 1] = z.y;
+      if (4 * qd + 2 < K) zv[4 * qd + 2] = z.z;
+      if (4 * qd + 3 < K) zv[4 * qd + 3] = z.w;
+    }
+    const bool ok = ws_cholesky(G, T, diag0, rinv, lane);
+    if (ok) {
+      // w = y + z with y = row K of L; u = L^-T w from the bottom
+      float v[4];
+      const int IK = K >> 3, pk = K & 7;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const int i = lane + 32 * mm;
+        v[mm] = i < K ? T[tidx(IK, i >> 3) * kWsTileF + pk * 8 + (i & 7)] + zv[i] : 0.f;
+      }
+      for (int k = K - 1; k >= 0; --k) {
+        const int owner = k & 31, mk = k >> 5;
+        float own = v[0];
+#pragma unroll
+        for (int mm = 1; mm < 4; ++mm)
+          if (mk == mm) own = v[mm];
+        const float uk = __shfl_sync(0xffffffffu, own, owner) * rinv[k];
+        const float* Lk = T + (k & 7) * 8;
+        const int Ik = k >> 3;
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+          const int i = lane + 32 * mm;
+          if (i == k) v[mm] = uk;
+          else if (i < k) v[mm] = fmaf(-Lk[tidx(Ik, i >> 3) * kWsTileF + (i & 7)], uk, v[mm]);
+        }
+      }
+      float* out = a.X + (int64_t)row * K;
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        const int i = lane + 32 * mm;
+        if (i < K) out[i] = v[mm];
+      }
+    } else if (lane == 0) {
+      a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&w.slot_empty[c]);
+  }
+}
+
+__global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C, int* counter,
+                                                 int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_ws[];
+  const WsGeom G(a.K);
+  const WsShared w = ws_carve(smem_ws, G, S, C);
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&w.full[s], kWsGather);
+      mbar_init(&w.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&w.acc_full[b], 1);
+      mbar_init(&w.acc_empty[b], kWsDrain);
+    }
+    for (int c = 0; c < C; ++c) {
+      mbar_init(&w.slot_full[c], kWsDrain);
+      mbar_init(&w.slot_empty[c], 1);
+    }
+    mbar_init(w.fin, 1);
+    mbar_init(w.row_ready, 1);
+    mbar_init(w.row_read, kWsGather);
+    *w.abort = 0;
+    mbar_fence_init();
+  }
+  // operand chunks past the last written one (features beyond K) stay zero
+  for (int e = threadIdx.x; e < S * kWsStageBytes / 16; e += blockDim.x)
+    reinterpret_cast<uint4*>(w.stages)[e] = make_uint4(0, 0, 0, 0);
+  if (warp == kWsMmaWarp) {
+    tmem_alloc(w.taddr, 2 * kWsAccCols);
+    tmem_relinquish();
+  }
+  if (warp >= 4 && warp < 8) ws_fill_base(a, G, w.base);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *w.taddr;
+  if (warp < 4) {
+    ws_gather(a, G, w, S, counter);
+  } else if (warp < 8) {
+    ws_drain(a, G, w, C, tmem);
+  } else if (warp == kWsMmaWarp) {
+    if ((threadIdx.x & 31) == 0) ws_mma(G, w, S, tmem);
+  } else if (warp - kWsConsWarp0 < C) {
+    ws_consume(a, G, w, C);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (*w.abort && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+  if (warp == kWsMmaWarp) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * kWsAccCols);
+  }
+}
+
+// bf16 hi/lo shadow of a factor matrix, rows padded to KS (a multiple of 8)
+__global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, int K, int KS,
+                                      __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = R * KS;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / KS;
+    const int c = (int)(e - r * KS);
+    const float x = c < K ? X[r * K + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+}  // namespace
+
+bool ws_supported(int K) { return K >= 8 && K + 1 <= 128; }
+
+int ws_config(int K, int* S, int* C) {
+  const WsGeom G(K);
+  int dev = 0, max_smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BPMF_ECUDA;
+  }
+  const int slot = G.slot_floats() * 4;
+  int c = kWsMaxCons;
+  while (c > 1 && ws_smem_bytes(G, 4, c) > max_smem) --c;
+  int s = kWsMaxStages;
+  while (s > 2 && ws_smem_bytes(G, s, c) > max_smem) --s;
+  if (ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
+  (void)slot;
+  *S = s;
+  *C = c;
+  return BPMF_OK;
+}
+
+int launch_rows_ws(const SweepArgs& a, int num_sms, int* counter, int* status, cudaStream_t st,
+                   int64_t* launches) {
+  const int64_t nrows = a.row_end - a.row_begin;
+  if (nrows <= 0) return BPMF_OK;
+  int S = 0, C = 0;
+  BPMF_TRY(ws_config(a.K, &S, &C));
+  const WsGeom G(a.K);
+  const int smem = ws_smem_bytes(G, S, C);
+  BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BPMF_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  const int grid = (int)std::min<int64_t>(num_sms, nrows);
+  row_ws<<<grid, 32 * (kWsConsWarp0 + C), smem, st>>>(a, S, C, counter, status);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  if (launches) *launches += 1;
+  return BPMF_OK;
+}
+
+int launch_refresh_shadow(Handle* h, int s) {
+  SideDev& sd = h->side[s];
+  if (!sd.Xhi || sd.R == 0) return BPMF_OK;
+  const int64_t total = sd.R * sd.KS;
+  int64_t g = (total + 255) / 256;
+  if (g > 16LL * h->num_sms) g = 16LL * h->num_sms;
+  refresh_shadow_kernel<<<(unsigned)g, 256, 0, h->stream>>>(sd.X, sd.R, h->K, sd.KS, sd.Xhi, sd.Xlo);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  h->kernels += 1;
+  return BPMF_OK;
+}
+
+}  // namespace gb

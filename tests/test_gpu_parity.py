@@ -126,19 +126,21 @@ def test_sweep_parity_split_hubs(gpu_lib, name, hub_min):
             assert rel_err(got, ref).max() <= TAU_FP32
 
 
+@pytest.mark.parametrize("heavy", [1, 2])
 @pytest.mark.parametrize("name,hub_min", [("powerlaw_k64", -1), ("powerlaw_k100", -1),
                                           ("powerlaw_k55", -1), ("uniform_k119", -1),
                                           ("powerlaw_k100", 90), ("powerlaw_k64", 60)])
-def test_sweep_parity_tensor_gram(gpu_lib, name, hub_min):
+def test_sweep_parity_tensor_gram(gpu_lib, name, hub_min, heavy):
     """Mixed path: bf16 hi/lo tcgen05 Gram (hi.hi + hi.lo + lo.hi, FP32
-    accumulation in tensor memory), FP32 Cholesky.  The contract is the BF16
+    accumulation in tensor memory), FP32 Cholesky; heavy rows on the
+    persistent warp-specialised kernel (1) or one CTA per row (2).  The contract is the BF16
     tolerance 1e-2; the split product is accurate to ~2^-16, so the observed
     error must also stay far below it (1e-3), which a missing cross term
     would break."""
     bp = gpu_lib
     ds, K, st = _case(name)
     U, V, hy, hyper = random_state(ds, K)
-    with _sampler(bp, ds, K, bp.PATH_MIXED, seed=17, hub_min=hub_min) as s:
+    with _sampler(bp, ds, K, bp.PATH_MIXED, seed=17, hub_min=hub_min, heavy_kernel=heavy) as s:
         for side in (0, 1):
             s.set_state(U, V, hyper, it=6)
             s.sweep(side)
