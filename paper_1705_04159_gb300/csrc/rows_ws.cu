@@ -51,7 +51,7 @@ constexpr int kWsOpBytes = 16 * kWsSBO;        // 128 features (the MMA reads M 
 constexpr int kWsStageBytes = 2 * kWsOpBytes;  // hi + lo
 constexpr int kWsMaxStages = 8;
 constexpr int kWsMaxCons = 7;
-constexpr int kWsRecs = 16;          // row records in flight: > stages + 2 (see the gather loop)
+constexpr int kWsRecs = 16;          // row records in flight (see the gather loop)
 constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (4 floats of skew against bank conflicts)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
@@ -174,18 +174,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-// wait until at most `n` (0..6) groups of this thread are pending
-__device__ __forceinline__ void cp_async_wait_dyn(int n) {
-  switch (n) {
-    case 0: cp_async_wait<0>(); break;
-    case 1: cp_async_wait<1>(); break;
-    case 2: cp_async_wait<2>(); break;
-    case 3: cp_async_wait<3>(); break;
-    case 4: cp_async_wait<4>(); break;
-    case 5: cp_async_wait<5>(); break;
-    default: cp_async_wait<6>(); break;
-  }
-}
+
 
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -197,23 +186,23 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
 }
 
 // ------------------------------------------------------------- gather --
-// Stage s receives neighbours [e, e + cnt) (cnt <= 16).  Thread t of the
-// gather group handles neighbour k = t % 16 and chunks c = t / 16 + 8 i, so
-// that 16 consecutive threads write 256 contiguous bytes.  Chunks 0 ..
+// The four gather warps take the stages of the row sequence in turn (stage n
+// by warp n % 4), so four stages are filled side by side.  In the warp that
+// fills stage n, lane l handles neighbour k = l % 16 and chunks c = l / 16 +
+// 2 i, so 16 consecutive lanes write 256 contiguous bytes.  Chunks 0 ..
 // ceil(K/8) - 1 are 16-byte copies of the shadow row (its padding past K is
 // zero); the rating (feature K, in chunk cb = K / 8) is patched in once the
 // copy of its chunk has landed (ws_patch_rating).  Rows k >= cnt are zeroed.
 __device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs& a,
-                                                uint8_t* stage, int cnt, int32_t j) {
-  const int t = threadIdx.x;  // 0 .. 127
-  const int k = t & 15;
+                                                uint8_t* stage, int cnt, int32_t j, int lane) {
+  const int k = lane & 15;
   const bool live = k < cnt;
   const __nv_bfloat16* hrow = a.Vhi + (int64_t)j * a.KS;
   const __nv_bfloat16* lrow = a.Vlo + (int64_t)j * a.KS;
   const uint32_t hi = smem_u32(stage), lo = hi + kWsOpBytes;
   const int koff = (k >> 3) * kWsLBO + (k & 7) * 16;
   const int ncopy = (G.K + 7) >> 3;
-  for (int c = t >> 4; c <= G.cb; c += 8) {
+  for (int c = lane >> 4; c <= G.cb; c += 2) {
     const int off = c * kWsSBO + koff;
     if (live && c < ncopy) {
       cp_async16(hi + off, hrow + 8 * c);
@@ -226,11 +215,11 @@ __device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs
 }
 
 // Feature K of neighbour k = the rating r, as bf16 hi and lo, written by the
-// thread that copied chunk cb of that neighbour after its copy completed.
-__device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r) {
-  const int t = threadIdx.x;
-  if ((t >> 4) != (G.cb & 7)) return;
-  const int k = t & 15;
+// lane that copied chunk cb of that neighbour, after its copy completed.
+__device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r,
+                                                int lane) {
+  if ((lane >> 4) != (G.cb & 1)) return;
+  const int k = lane & 15;
   const int off = G.cb * kWsSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
   const __nv_bfloat16 h = __float2bfloat16_rn(r);
   *reinterpret_cast<__nv_bfloat16*>(stage + off) = h;
@@ -238,19 +227,27 @@ __device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage,
       __float2bfloat16_rn(r - __bfloat162float(h));
 }
 
+// Copies of a warp's previous stage are waited for, patched, made visible to
+// the tensor cores and signalled once its next stage has been issued.
+__device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
+                                          int lane) {
+  const int ss = (int)(m % (uint32_t)S);
+  ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + (lane & 15)], lane);
+  fence_proxy_async_smem();
+  mbar_arrive(&w.full[ss]);
+}
+
 __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
                                           int S, int* counter) {
   const int t = threadIdx.x;
-  const int k = t & 15;
-  const bool patcher = (t >> 4) == (G.cb & 7);
+  const int wg = t >> 5, lane = t & 31, k = lane & 15;
+  const bool patcher = (lane >> 4) == (G.cb & 1);
   const int nrows = (int)(a.row_end - a.row_begin);
-  uint32_t n = 0;          // stage sequence number
-  int q = 0;               // row sequence number
-  // copies of up to S - 1 stages are in flight; stage n is signalled full
-  // once stage n + S - 2 has been issued (the ring keeps one stage spare,
-  // so the gather never waits for a stage it has not yet signalled)
-  const int lag = S - 2;
-  uint32_t signalled = 0;  // stages [0, signalled) have been signalled
+  // with six or more stages a warp keeps two of its stages in flight
+  const bool lag1 = S >= 6;
+  uint32_t n = 0;             // stage sequence number (the same in every gather warp)
+  int q = 0;                  // row sequence number
+  uint32_t pend = 0xffffffffu;  // this warp's issued stage not yet signalled
   // thread 0 prefetches the next row's work entry (row, first, last rating)
   int4 wk = make_int4(-1, 0, 0, 0);
   int next_slot = 0;
@@ -258,6 +255,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
     next_slot = atomicAdd(counter, 1);
     if (next_slot < nrows) wk = __ldg(a.work + a.row_begin + next_slot);
   }
+  bool stop = false;
   for (;;) {
     if (t == 0) {
       // the slot is free once every gather thread has read the previous row
@@ -266,42 +264,33 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
       w.next_row[1] = wk.y;
       w.next_row[2] = wk.z;
       mbar_arrive(w.row_ready);
-      if (ok && wk.x >= 0) next_slot = atomicAdd(counter, 1);  // used after the first stage
+      if (ok && wk.x >= 0) next_slot = atomicAdd(counter, 1);
     }
     if (!ws_wait_warp(w.row_ready, (uint32_t)q & 1u, w.abort)) break;
     const int row = w.next_row[0];
     const int e0 = w.next_row[1], e1 = row >= 0 ? w.next_row[2] : e0;
     mbar_arrive(w.row_read);
+    if (t == 0)
+      wk = next_slot < nrows && row >= 0 ? __ldg(a.work + a.row_begin + next_slot)
+                                         : make_int4(-1, 0, 0, 0);
     const int nst_r = (e1 - e0 + kWsNb - 1) / kWsNb;
     const int nst = nst_r > 0 ? nst_r : 1;
-    // neighbour id and rating of this thread for the current stage, loaded a
-    // stage ahead
-    int32_t jc = 0;
-    float rc = 0.f;
-    if (row >= 0 && k < e1 - e0) {
-      jc = __ldg(a.idx + e0 + k);
-      rc = __ldg(a.val + e0 + k);
-    }
-    bool stop = false;
-    for (int st = 0; st < nst; ++st) {
-      const int s = (int)(n % (uint32_t)S);
+    for (int st = (int)((uint32_t)(wg - (int)(n & 3u)) & 3u); st < nst; st += 4) {
+      const uint32_t nn = n + (uint32_t)st;
+      const int s = (int)(nn % (uint32_t)S);
       const int e = e0 + st * kWsNb;
       const int cnt = row < 0 ? 0 : (e1 - e < kWsNb ? (e1 - e > 0 ? e1 - e : 0) : kWsNb);
-      int32_t jn = 0;
-      float rn = 0.f;
-      if (st + 1 < nst && k < e1 - e - kWsNb) {
-        jn = __ldg(a.idx + e + kWsNb + k);
-        rn = __ldg(a.val + e + kWsNb + k);
+      int32_t j = 0;
+      float r = 0.f;
+      if (k < cnt) {
+        j = __ldg(a.idx + e + k);
+        r = __ldg(a.val + e + k);
       }
-      if (t == 0 && st == 0 && next_slot < nrows && row >= 0)
-        wk = __ldg(a.work + a.row_begin + next_slot);
-      else if (t == 0 && st == 0)
-        wk = make_int4(-1, 0, 0, 0);
-      if (!ws_wait_warp(&w.empty[s], ((n / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
+      if (!ws_wait_warp(&w.empty[s], ((nn / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
         stop = true;
         break;
       }
-      if (t == 0) {
+      if (lane == 0) {
         if (st == 0) {
           w.recs[q % kWsRecs].row = row;
           w.recs[q % kWsRecs].nst = row < 0 ? 0 : nst_r;
@@ -310,31 +299,26 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
         w.meta[s].cnt = cnt;
         w.meta[s].flags = (st == 0 ? 1 : 0) | (st == nst - 1 ? 2 : 0);
       }
-      if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, jc);
-      if (patcher) w.rating[s * kWsNb + k] = k < cnt ? rc : 0.f;
+      if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, j, lane);
+      if (patcher) w.rating[s * kWsNb + k] = k < cnt ? r : 0.f;
       cp_async_commit();
-      ++n;
-      if (n - signalled > (uint32_t)lag) {
-        cp_async_wait_dyn(lag);
-        const int ss = (int)(signalled % (uint32_t)S);
-        ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + k]);
-        fence_proxy_async_smem();
-        mbar_arrive(&w.full[ss]);
-        ++signalled;
+      if (lag1) {
+        if (pend != 0xffffffffu) {
+          cp_async_wait<1>();
+          ws_signal(G, w, S, pend, lane);
+        }
+        pend = nn;
+      } else {
+        cp_async_wait<0>();
+        ws_signal(G, w, S, nn, lane);
       }
-      jc = jn;
-      rc = rn;
     }
+    n += (uint32_t)nst;
     if (stop || row < 0) break;
     ++q;
   }
   cp_async_wait<0>();
-  for (; signalled < n; ++signalled) {
-    const int ss = (int)(signalled % (uint32_t)S);
-    ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + k]);
-    fence_proxy_async_smem();
-    mbar_arrive(&w.full[ss]);
-  }
+  if (pend != 0xffffffffu) ws_signal(G, w, S, pend, lane);
 }
 
 // ---------------------------------------------------------------- MMA --
@@ -491,14 +475,17 @@ __device__ __forceinline__ int tidx(int I, int J) { return I * (I + 1) / 2 + J; 
 __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const float* diag0, float* rinv, int lane) {
   bool fail = false;
   for (int p = 0; p < G.g; ++p) {
-    // (a) diagonal tile: lane r < 8 holds row r
+    // (a) diagonal tile, factored by every lane in registers (the same
+    // values in all lanes: no shuffles), rows written back by lanes 0-7
     float* D = T + tidx(p, p) * kWsTileF;
-    float r[8];
-    ld8(D + (lane & 7) * 8, r);
+    float d[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ld8(D + i * 8, d[i]);
+    float rdv[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int idx = 8 * p + c;
-      float piv = __shfl_sync(0xffffffffu, r[c], c);
+      float piv = d[c][c];
       if (idx < G.K) {
         const float d0 = diag0[idx];
         if (!(piv > kPivotRel * d0)) {
@@ -509,21 +496,24 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
         piv = fmaxf(piv, FLT_MIN);  // row K (never used as a pivot) or padding (1)
       }
       const float rd = rsqrtf(piv);
-      if (lane == c) {
-        r[c] = piv * rd;
-        rinv[idx] = rd;
-      } else if (lane > c) {
-        r[c] *= rd;
-      }
+      rdv[c] = rd;
+      d[c][c] = piv * rd;
 #pragma unroll
-      for (int s2 = c + 1; s2 < 8; ++s2) {
-        const float ls = __shfl_sync(0xffffffffu, r[c], s2);
-        if (lane >= s2) r[s2] = fmaf(-r[c], ls, r[s2]);
-      }
+      for (int i = c + 1; i < 8; ++i) d[i][c] *= rd;
+#pragma unroll
+      for (int j2 = c + 1; j2 < 8; ++j2)
+#pragma unroll
+        for (int i = j2; i < 8; ++i) d[i][j2] = fmaf(-d[i][c], d[j2][c], d[i][j2]);
     }
-    if (lane < 8) st8(D + lane * 8, r);
-    __syncwarp();
-    // (b) panel rows below: x L_pp^T = a, row by row
+    if (lane < 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (lane == i) st8(D + i * 8, d[i]);
+      rinv[8 * p + lane] = lane == 0 ? rdv[0] : lane == 1 ? rdv[1] : lane == 2 ? rdv[2] :
+                           lane == 3 ? rdv[3] : lane == 4 ? rdv[4] : lane == 5 ? rdv[5] :
+                           lane == 6 ? rdv[6] : rdv[7];
+    }
+    // (b) panel rows below: x L_pp^T = a, row by row, against the registers
     const int nb = G.g - 1 - p;
     for (int rr = lane; rr < 8 * nb; rr += 32) {
       const int I = p + 1 + (rr >> 3);
@@ -532,12 +522,10 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
       ld8(row, x);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        float dr[8];
-        ld8(D + c * 8, dr);
-        float t = x[c];
+        float t2 = x[c];
 #pragma unroll
-        for (int s2 = 0; s2 < c; ++s2) t = fmaf(-x[s2], dr[s2], t);
-        x[c] = t * rinv[8 * p + c];
+        for (int s2 = 0; s2 < c; ++s2) t2 = fmaf(-x[s2], d[c][s2], t2);
+        x[c] = t2 * rdv[c];
       }
       st8(row, x);
     }
@@ -598,7 +586,10 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
     }
     const bool ok = ws_cholesky(G, T, diag0, rinv, lane);
     if (ok) {
-      // w = y + z with y = row K of L; u = L^-T w from the bottom
+      // w = y + z with y = row K of L; u = L^-T w by 8-row blocks from the
+      // bottom: every lane solves the block's 8 x 8 system against the
+      // diagonal tile in registers, then subtracts the block's contribution
+      // from the w_i it owns (i = lane + 32 mm)
       float v[4];
       const int IK = K >> 3, pk = K & 7;
 #pragma unroll
@@ -606,20 +597,40 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
         const int i = lane + 32 * mm;
         v[mm] = i < K ? T[tidx(IK, i >> 3) * kWsTileF + pk * 8 + (i & 7)] + zv[i] : 0.f;
       }
-      for (int k = K - 1; k >= 0; --k) {
-        const int owner = k & 31, mk = k >> 5;
+      for (int I = (K - 1) >> 3; I >= 0; --I) {
+        const int mI = I >> 2, l0 = (I & 3) * 8;  // rows 8I.. live in v[mI] of lanes l0..l0+7
         float own = v[0];
 #pragma unroll
         for (int mm = 1; mm < 4; ++mm)
-          if (mk == mm) own = v[mm];
-        const float uk = __shfl_sync(0xffffffffu, own, owner) * rinv[k];
-        const float* Lk = T + (k & 7) * 8;
-        const int Ik = k >> 3;
+          if (mI == mm) own = v[mm];
+        float wb[8], u[8];
+#pragma unroll
+        for (int q2 = 0; q2 < 8; ++q2) wb[q2] = __shfl_sync(0xffffffffu, own, l0 + q2);
+        const float* Dg = T + tidx(I, I) * kWsTileF;
+        const int nI = K - 8 * I < 8 ? K - 8 * I : 8;
+#pragma unroll
+        for (int c = 7; c >= 0; --c) {
+          float t2 = wb[c];
+#pragma unroll
+          for (int r2 = c + 1; r2 < 8; ++r2) t2 = fmaf(-Dg[r2 * 8 + c], u[r2], t2);
+          u[c] = c < nI ? t2 * rinv[8 * I + c] : 0.f;
+        }
+        // the block's solution goes through shared memory (z of these rows
+        // is no longer needed) to the lanes that own its rows
+        if (lane == 0) st8(zv + 8 * I, u);
+        __syncwarp();
 #pragma unroll
         for (int mm = 0; mm < 4; ++mm) {
           const int i = lane + 32 * mm;
-          if (i == k) v[mm] = uk;
-          else if (i < k) v[mm] = fmaf(-Lk[tidx(Ik, i >> 3) * kWsTileF + (i & 7)], uk, v[mm]);
+          if (i >= 8 * I && i < 8 * I + 8) {
+            v[mm] = zv[i];
+          } else if (i < 8 * I) {
+            const float* Lc = T + tidx(I, i >> 3) * kWsTileF + (i & 7);
+            float t2 = v[mm];
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) t2 = fmaf(-Lc[q2 * 8], u[q2], t2);
+            v[mm] = t2;
+          }
         }
       }
       float* out = a.X + (int64_t)row * K;
@@ -644,7 +655,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&w.full[s], kWsGather);
+      mbar_init(&w.full[s], 32);  // the lanes of the warp that fills the stage
       mbar_init(&w.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
