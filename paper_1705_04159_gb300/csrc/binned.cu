@@ -52,7 +52,8 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
     r.row_begin = e_hub;
     r.row_end = e_heavy;
     if (sd.Xhi && ws_supported(h->K) && !sd.heavy_tc)
-      BPMF_TRY(launch_rows_ws(r, h->num_sms, h->ws_counter, h->status, st, &h->kernels));
+      BPMF_TRY(launch_rows_ws(r, h->num_sms, sd.ws_cons, h->ws_counter, h->status, st,
+                              &h->kernels));
     else if (tc)
       BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
     else

@@ -66,7 +66,8 @@ struct SideDev {
   std::vector<int64_t> ptr_h;   // host: row pointers
   std::vector<int32_t> perm_h;  // host: degree order
   int64_t max_deg = 0;
-  bool heavy_tc = false;  // heavy bin on the per-row tensor-core kernel instead of the persistent one
+  bool heavy_tc = false;
+  int ws_cons = 0;        // consumer warps of the persistent kernel (0: automatic)  // heavy bin on the per-row tensor-core kernel instead of the persistent one
   bool have_hyper = false;
   bool have_stats = false;
   int64_t fp64_rows = 0;

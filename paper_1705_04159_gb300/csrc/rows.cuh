@@ -57,8 +57,9 @@ int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStrea
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 // heavy rows by the persistent warp-specialised kernel (rows_ws.cu)
 bool ws_supported(int K);
-int launch_rows_ws(const SweepArgs& a, int num_sms, int* counter, int* status, cudaStream_t st,
-                   int64_t* launches);
+// cons: consumer warps per CTA (0: automatic)
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int* counter, int* status,
+                   cudaStream_t st, int64_t* launches);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
 int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
 

@@ -10,10 +10,10 @@
 // One CTA per SM takes rows of the degree order from a global counter
 // (largest first) and runs them through a pipeline of warp roles:
 //   gather (warps 0-3): copies the bf16 hi/lo shadow rows of the neighbours,
-//     16 per stage, with 16-byte cp.async straight into MN-major operand
+//     32 per stage, with 16-byte cp.async straight into MN-major operand
 //     tiles (feature-contiguous 8 x 16-byte core matrices: chunk c of
-//     neighbour k at c * 256 + (k / 8) * 128 + (k % 8) * 16), plus the
-//     chunk holding the rating feature, into a ring of stages;
+//     neighbour k at c * 512 + (k / 8) * 128 + (k % 8) * 16) into a ring of
+//     stages, and patches the rating in as feature K;
 //   MMA (warp 8, one thread): per stage hi.hi + hi.lo + lo.hi into one of two
 //     FP32 accumulators in tensor memory (G = X^T X with X the stage's
 //     neighbours x features; lo.lo, ~2^-16 relative, is dropped);
@@ -44,14 +44,14 @@
 namespace gb {
 namespace {
 
-constexpr int kWsNb = 16;            // neighbours per stage (one MMA K-step)
-constexpr int kWsLBO = 128;          // operand tiles: bytes between the two 8-neighbour groups
-constexpr int kWsSBO = 256;          //   and between 8-feature chunks
+constexpr int kWsNb = 32;            // neighbours per stage (two MMA K-steps)
+constexpr int kWsLBO = 128;          // operand tiles: bytes between 8-neighbour groups
+constexpr int kWsSBO = kWsNb * 16;   //   and between 8-feature chunks
 constexpr int kWsOpBytes = 16 * kWsSBO;        // 128 features (the MMA reads M = 128 rows)
 constexpr int kWsStageBytes = 2 * kWsOpBytes;  // hi + lo
-constexpr int kWsMaxStages = 8;
+constexpr int kWsMaxStages = 16;
 constexpr int kWsMaxCons = 7;
-constexpr int kWsRecs = 16;          // row records in flight (see the gather loop)
+constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (see the gather loop)
 constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (4 floats of skew against bank conflicts)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
@@ -188,21 +188,21 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
 // ------------------------------------------------------------- gather --
 // The four gather warps take the stages of the row sequence in turn (stage n
 // by warp n % 4), so four stages are filled side by side.  In the warp that
-// fills stage n, lane l handles neighbour k = l % 16 and chunks c = l / 16 +
-// 2 i, so 16 consecutive lanes write 256 contiguous bytes.  Chunks 0 ..
+// fills stage n, lane l handles neighbour l and every chunk c of it, so the
+// warp writes chunk c of all 32 neighbours as 512 contiguous bytes.  Chunks 0 ..
 // ceil(K/8) - 1 are 16-byte copies of the shadow row (its padding past K is
 // zero); the rating (feature K, in chunk cb = K / 8) is patched in once the
 // copy of its chunk has landed (ws_patch_rating).  Rows k >= cnt are zeroed.
 __device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs& a,
                                                 uint8_t* stage, int cnt, int32_t j, int lane) {
-  const int k = lane & 15;
+  const int k = lane;
   const bool live = k < cnt;
   const __nv_bfloat16* hrow = a.Vhi + (int64_t)j * a.KS;
   const __nv_bfloat16* lrow = a.Vlo + (int64_t)j * a.KS;
   const uint32_t hi = smem_u32(stage), lo = hi + kWsOpBytes;
   const int koff = (k >> 3) * kWsLBO + (k & 7) * 16;
   const int ncopy = (G.K + 7) >> 3;
-  for (int c = lane >> 4; c <= G.cb; c += 2) {
+  for (int c = 0; c <= G.cb; ++c) {
     const int off = c * kWsSBO + koff;
     if (live && c < ncopy) {
       cp_async16(hi + off, hrow + 8 * c);
@@ -218,8 +218,7 @@ __device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs
 // lane that copied chunk cb of that neighbour, after its copy completed.
 __device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r,
                                                 int lane) {
-  if ((lane >> 4) != (G.cb & 1)) return;
-  const int k = lane & 15;
+  const int k = lane;
   const int off = G.cb * kWsSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
   const __nv_bfloat16 h = __float2bfloat16_rn(r);
   *reinterpret_cast<__nv_bfloat16*>(stage + off) = h;
@@ -232,7 +231,7 @@ __device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage,
 __device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
                                           int lane) {
   const int ss = (int)(m % (uint32_t)S);
-  ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + (lane & 15)], lane);
+  ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + lane], lane);
   fence_proxy_async_smem();
   mbar_arrive(&w.full[ss]);
 }
@@ -240,8 +239,7 @@ __device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, in
 __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
                                           int S, int* counter) {
   const int t = threadIdx.x;
-  const int wg = t >> 5, lane = t & 31, k = lane & 15;
-  const bool patcher = (lane >> 4) == (G.cb & 1);
+  const int wg = t >> 5, lane = t & 31, k = lane;
   const int nrows = (int)(a.row_end - a.row_begin);
   // with six or more stages a warp keeps two of its stages in flight
   const bool lag1 = S >= 6;
@@ -275,16 +273,25 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
                                          : make_int4(-1, 0, 0, 0);
     const int nst_r = (e1 - e0 + kWsNb - 1) / kWsNb;
     const int nst = nst_r > 0 ? nst_r : 1;
-    for (int st = (int)((uint32_t)(wg - (int)(n & 3u)) & 3u); st < nst; st += 4) {
+    const int st_first = (int)((uint32_t)(wg - (int)(n & 3u)) & 3u);
+    // neighbour id and rating of this lane for the warp's next stage (four
+    // stages on), loaded while the current one is issued
+    int32_t jn = 0;
+    float rn = 0.f;
+    if (row >= 0 && st_first < nst && e0 + st_first * kWsNb + k < e1) {
+      jn = __ldg(a.idx + e0 + st_first * kWsNb + k);
+      rn = __ldg(a.val + e0 + st_first * kWsNb + k);
+    }
+    for (int st = st_first; st < nst; st += 4) {
       const uint32_t nn = n + (uint32_t)st;
       const int s = (int)(nn % (uint32_t)S);
       const int e = e0 + st * kWsNb;
       const int cnt = row < 0 ? 0 : (e1 - e < kWsNb ? (e1 - e > 0 ? e1 - e : 0) : kWsNb);
-      int32_t j = 0;
-      float r = 0.f;
-      if (k < cnt) {
-        j = __ldg(a.idx + e + k);
-        r = __ldg(a.val + e + k);
+      const int32_t j = jn;
+      const float r = rn;
+      if (row >= 0 && e + 4 * kWsNb + k < e1) {
+        jn = __ldg(a.idx + e + 4 * kWsNb + k);
+        rn = __ldg(a.val + e + 4 * kWsNb + k);
       }
       if (!ws_wait_warp(&w.empty[s], ((nn / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
         stop = true;
@@ -300,7 +307,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
         w.meta[s].flags = (st == 0 ? 1 : 0) | (st == nst - 1 ? 2 : 0);
       }
       if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, j, lane);
-      if (patcher) w.rating[s * kWsNb + k] = k < cnt ? r : 0.f;
+      w.rating[s * kWsNb + k] = k < cnt ? r : 0.f;
       cp_async_commit();
       if (lag1) {
         if (pend != 0xffffffffu) {
@@ -341,11 +348,14 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
     const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
     if (m.cnt > 0) {
       const uint32_t hi = base + (uint32_t)s * kWsStageBytes, lo = hi + kWsOpBytes;
-      const uint64_t dh = smem_desc_kmajor(hi, kWsLBO, kWsSBO);
-      const uint64_t dl = smem_desc_kmajor(lo, kWsLBO, kWsSBO);
-      tc_mma_bf16(acc, dh, dh, idesc, (m.flags & 1) ? 0u : 1u);
-      tc_mma_bf16(acc, dh, dl, idesc, 1u);
-      tc_mma_bf16(acc, dl, dh, idesc, 1u);
+      // K-steps of 16 neighbours: two 8-neighbour groups (2 LBO) apart
+      for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
+        const uint64_t dh = smem_desc_kmajor(hi + kk * 2 * kWsLBO, kWsLBO, kWsSBO);
+        const uint64_t dl = smem_desc_kmajor(lo + kk * 2 * kWsLBO, kWsLBO, kWsSBO);
+        tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
+        tc_mma_bf16(acc, dh, dl, idesc, 1u);
+        tc_mma_bf16(acc, dl, dh, idesc, 1u);
+      }
     }
     tc_commit(&w.empty[s]);
     ++n;
@@ -530,32 +540,48 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
       st8(row, x);
     }
     __syncwarp();
-    // (c) trailing tiles (I, J), p < J <= I: A_IJ -= L_Ip L_Jp^T
+    // (c) trailing tiles (I, J), p < J <= I: A_IJ -= L_Ip L_Jp^T, in units
+    // of half a tile (4 of its 8 columns) so that more lanes have work; the
+    // rows of L_Ip and A_IJ are loaded one row ahead
     const int ntl = nb * (nb + 1) / 2;
-    for (int tt = lane; tt < ntl; tt += 32) {
+    for (int u2 = lane; u2 < 2 * ntl; u2 += 32) {
+      const int tt = u2 >> 1, h = u2 & 1;
       int i0 = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
       while ((i0 + 1) * (i0 + 2) / 2 <= tt) ++i0;
       while (i0 * (i0 + 1) / 2 > tt) --i0;
       const int I = p + 1 + i0, J = p + 1 + (tt - i0 * (i0 + 1) / 2);
       const float* LI = T + tidx(I, p) * kWsTileF;
-      const float* LJ = T + tidx(J, p) * kWsTileF;
-      float* A = T + tidx(I, J) * kWsTileF;
-      float lj[8][8];
+      const float* LJ = T + tidx(J, p) * kWsTileF + 32 * h;
+      float* A = T + tidx(I, J) * kWsTileF + 4 * h;
+      float lj[4][8];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) ld8(LJ + jj * 8, lj[jj]);
+      for (int jj = 0; jj < 4; ++jj) ld8(LJ + jj * 8, lj[jj]);
+      float li[8];
+      float4 ar;
+      ld8(LI, li);
+      ar = *reinterpret_cast<const float4*>(A);
 #pragma unroll
       for (int ii = 0; ii < 8; ++ii) {
-        float li[8], ar[8];
-        ld8(LI + ii * 8, li);
-        ld8(A + ii * 8, ar);
+        float lin[8];
+        float4 arn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ii < 7) {
+          ld8(LI + (ii + 1) * 8, lin);
+          arn = *reinterpret_cast<const float4*>(A + (ii + 1) * 8);
+        }
+        float a4[4] = {ar.x, ar.y, ar.z, ar.w};
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          float s3 = ar[jj];
+        for (int jj = 0; jj < 4; ++jj) {
+          float s3 = a4[jj];
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) s3 = fmaf(-li[kk], lj[jj][kk], s3);
-          ar[jj] = s3;
+          a4[jj] = s3;
         }
-        st8(A + ii * 8, ar);
+        *reinterpret_cast<float4*>(A + ii * 8) = make_float4(a4[0], a4[1], a4[2], a4[3]);
+        if (ii < 7) {
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) li[kk] = lin[kk];
+          ar = arn;
+        }
       }
     }
     __syncwarp();
@@ -722,7 +748,12 @@ __global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, in
 
 bool ws_supported(int K) { return K >= 8 && K + 1 <= 128; }
 
-int ws_config(int K, int* S, int* C) {
+// Stages and consumer warps for latent dimension K.  With `cons` > 0 that
+// many consumers (if they fit); otherwise the ring gets 6 stages (the
+// gather-to-MMA round trip is long: a deep ring hides it) and the consumers
+// take the rest of shared memory, at least 3 of them if the ring can give
+// way down to 4 stages.
+int ws_config(int K, int cons, int* S, int* C) {
   const WsGeom G(K);
   int dev = 0, max_smem = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -730,24 +761,36 @@ int ws_config(int K, int* S, int* C) {
     cudaGetLastError();
     return BPMF_ECUDA;
   }
-  const int slot = G.slot_floats() * 4;
-  int c = kWsMaxCons;
-  while (c > 1 && ws_smem_bytes(G, 4, c) > max_smem) --c;
-  int s = kWsMaxStages;
-  while (s > 2 && ws_smem_bytes(G, s, c) > max_smem) --s;
-  if (ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
-  (void)slot;
+  auto fit_cons = [&](int s) {
+    int c = kWsMaxCons;
+    while (c > 0 && ws_smem_bytes(G, s, c) > max_smem) --c;
+    return c;
+  };
+  int s = 6, c = 0;
+  if (cons > 0) {
+    c = std::min(cons, kWsMaxCons);
+    s = kWsMaxStages;
+    while (s > 2 && ws_smem_bytes(G, s, c) > max_smem) --s;
+    if (s > 8) s = 8;
+  } else {
+    c = fit_cons(s);
+    if (c < 3) {
+      s = 4;
+      c = fit_cons(s);
+    }
+  }
+  if (c < 1 || s < 2 || ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
   *S = s;
   *C = c;
   return BPMF_OK;
 }
 
-int launch_rows_ws(const SweepArgs& a, int num_sms, int* counter, int* status, cudaStream_t st,
-                   int64_t* launches) {
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int* counter, int* status,
+                   cudaStream_t st, int64_t* launches) {
   const int64_t nrows = a.row_end - a.row_begin;
   if (nrows <= 0) return BPMF_OK;
   int S = 0, C = 0;
-  BPMF_TRY(ws_config(a.K, &S, &C));
+  BPMF_TRY(ws_config(a.K, cons, &S, &C));
   const WsGeom G(a.K);
   const int smem = ws_smem_bytes(G, S, C);
   BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
