@@ -285,6 +285,7 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
       sd.heavy_tc = it->second[3] != 0;
+      sd.ws_cons = (int)it->second[4];
       return apply_bins(h, s, it->second[0], it->second[1], it->second[2]);
     }
   }
@@ -299,6 +300,24 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     sd.heavy_tc = true;
     BPMF_TRY(time_sweep(h, s, scratch, reps, &t_tc));
     sd.heavy_tc = t_tc < t_ws;
+  }
+  if (!sd.heavy_tc && h->cfg.path == BPMF_PATH_MIXED && ws_supported(h->K) && sd.Xhi) {
+    // consumer warps of the persistent kernel: fewer leave room for a deeper
+    // stage ring (rows with many ratings), more factor more rows at once
+    int best_c = 0;
+    float best = 3.0e38f;
+    for (int c : {0, 2, 3, 4, 5, 6}) {
+      sd.ws_cons = c;
+      if (time_sweep(h, s, scratch, reps, &ms) != BPMF_OK) {
+        cudaGetLastError();  // that many consumers do not fit: not a candidate
+        continue;
+      }
+      if (ms < best) {
+        best = ms;
+        best_c = c;
+      }
+    }
+    sd.ws_cons = best_c;
   }
   const int64_t maxdeg = sd.deg_h.empty() ? 0 : sd.deg_h[0];
   if (h->cfg.hub_min < 0 && maxdeg >= 2048) {
@@ -350,7 +369,7 @@ int autotune_bins(Handle* h, int s, float* scratch) {
   sd.have_hyper = false;
   sd.have_stats = false;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[key] = {sd.tiny_max, sd.light_max, sd.hub_min, sd.heavy_tc ? 1 : 0};
+  g_tuned[key] = {sd.tiny_max, sd.light_max, sd.hub_min, sd.heavy_tc ? 1 : 0, sd.ws_cons};
   return BPMF_OK;
 }
 

@@ -226,11 +226,19 @@ __device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage,
       __float2bfloat16_rn(r - __bfloat162float(h));
 }
 
+// Stage n lives in ring slot (n % 4) + 4 ((n / 4) % (S / 4)) (S is a
+// multiple of 4): every slot is filled by one gather warp only, in order, so
+// no warp ever waits on a slot's barrier more than one phase ahead (an
+// mbarrier wait tells phases apart by parity only).
+__host__ __device__ __forceinline__ int ws_slot(uint32_t n, int S) {
+  return (int)(n & 3u) + 4 * (int)((n >> 2) % (uint32_t)(S >> 2));
+}
+
 // Copies of a warp's previous stage are waited for, patched, made visible to
 // the tensor cores and signalled once its next stage has been issued.
 __device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
                                           int lane) {
-  const int ss = (int)(m % (uint32_t)S);
+  const int ss = ws_slot(m, S);
   ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + lane], lane);
   fence_proxy_async_smem();
   mbar_arrive(&w.full[ss]);
@@ -241,8 +249,9 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   const int t = threadIdx.x;
   const int wg = t >> 5, lane = t & 31, k = lane;
   const int nrows = (int)(a.row_end - a.row_begin);
-  // with six or more stages a warp keeps two of its stages in flight
-  const bool lag1 = S >= 6;
+  // with eight or more stages (two or more slots per warp) a warp keeps two
+  // of its stages in flight
+  const bool lag1 = S >= 8;
   uint32_t n = 0;             // stage sequence number (the same in every gather warp)
   int q = 0;                  // row sequence number
   uint32_t pend = 0xffffffffu;  // this warp's issued stage not yet signalled
@@ -284,7 +293,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
     }
     for (int st = st_first; st < nst; st += 4) {
       const uint32_t nn = n + (uint32_t)st;
-      const int s = (int)(nn % (uint32_t)S);
+      const int s = ws_slot(nn, S);
       const int e = e0 + st * kWsNb;
       const int cnt = row < 0 ? 0 : (e1 - e < kWsNb ? (e1 - e > 0 ? e1 - e : 0) : kWsNb);
       const int32_t j = jn;
@@ -335,7 +344,7 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
   uint32_t n = 0;
   int q = 0;
   for (;;) {
-    const int s = (int)(n % (uint32_t)S);
+    const int s = ws_slot(n, S);
     if (!ws_wait(&w.full[s], (n / (uint32_t)S) & 1u, w.abort)) break;
     tc_fence_after();
     const StageMeta m = w.meta[s];
@@ -748,11 +757,11 @@ __global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, in
 
 bool ws_supported(int K) { return K >= 8 && K + 1 <= 128; }
 
-// Stages and consumer warps for latent dimension K.  With `cons` > 0 that
-// many consumers (if they fit); otherwise the ring gets 6 stages (the
-// gather-to-MMA round trip is long: a deep ring hides it) and the consumers
-// take the rest of shared memory, at least 3 of them if the ring can give
-// way down to 4 stages.
+// Stages (a multiple of 4, one or more ring slots per gather warp) and
+// consumer warps for latent dimension K.  With `cons` > 0 that many
+// consumers (if they fit) and the deepest ring up to 8 stages that fits;
+// otherwise 8 stages if at least 3 consumers fit beside them, else 4 stages
+// and as many consumers as fit.
 int ws_config(int K, int cons, int* S, int* C) {
   const WsGeom G(K);
   int dev = 0, max_smem = 0;
@@ -766,12 +775,10 @@ int ws_config(int K, int cons, int* S, int* C) {
     while (c > 0 && ws_smem_bytes(G, s, c) > max_smem) --c;
     return c;
   };
-  int s = 6, c = 0;
+  int s = 8, c = 0;
   if (cons > 0) {
     c = std::min(cons, kWsMaxCons);
-    s = kWsMaxStages;
-    while (s > 2 && ws_smem_bytes(G, s, c) > max_smem) --s;
-    if (s > 8) s = 8;
+    if (ws_smem_bytes(G, s, c) > max_smem) s = 4;
   } else {
     c = fit_cons(s);
     if (c < 3) {
@@ -779,7 +786,7 @@ int ws_config(int K, int cons, int* S, int* C) {
       c = fit_cons(s);
     }
   }
-  if (c < 1 || s < 2 || ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
+  if (c < 1 || ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
   *S = s;
   *C = c;
   return BPMF_OK;
