@@ -205,11 +205,14 @@ BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
  * Errors: EINVAL. */
 BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *fp64_rows);
 
-/* The degree thresholds in effect for `side`: thresholds[0] = tiny_max
- * (-1: no rank-one bin), [1] = light_max, [2] = hub_min -- the configured
- * values, the defaults (tiny_max 0 on the BINNED and MIXED paths, light_max =
- * tiny_max, hub_min 8192) or the autotuned ones.  Errors: EINVAL. */
-BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[3]);
+/* The schedule in effect for `side`: thresholds[0] = tiny_max (-1: no
+ * rank-one bin), [1] = light_max, [2] = hub_min -- the configured values, the
+ * defaults (tiny_max 0 on the BINNED and MIXED paths, light_max = tiny_max,
+ * hub_min 8192) or the autotuned ones; [3] = the kernel of the heavy bin (0
+ * FP32 CTA per row, 1 persistent warp-specialised, 2 tensor-core CTA per
+ * row); [4] = consumer warps of the persistent kernel (0: automatic).
+ * Errors: EINVAL. */
+BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[5]);
 
 /* ---- kernel timers (bpmf_get_timing) ---- */
 #define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */

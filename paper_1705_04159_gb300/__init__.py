@@ -317,8 +317,8 @@ def bpmf_set_timing(h, enable=True):
 
 
 def bpmf_get_thresholds(h, side):
-    """(tiny_max, light_max, hub_min) in effect for `side`."""
-    t = np.zeros(3, np.int64)
+    """(tiny_max, light_max, hub_min, heavy kernel, persistent consumers) of `side`."""
+    t = np.zeros(5, np.int64)
     _check(lib().bpmf_get_thresholds(h, side, t.ctypes.data), "bpmf_get_thresholds")
     return tuple(int(x) for x in t)
 

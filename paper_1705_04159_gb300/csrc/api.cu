@@ -647,13 +647,17 @@ int bpmf_get_hyper_stats(bpmf_t* hh, int side, double* xbar, double* S) {
   return BPMF_OK;
 }
 
-int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[3]) {
+int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[5]) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !valid_side(side) || !thresholds) return BPMF_EINVAL;
   const SideDev& sd = h->side[side];
   thresholds[0] = sd.tiny_max;
   thresholds[1] = sd.light_max;
   thresholds[2] = sd.hub_min;
+  const bool mixed = h->cfg.path == BPMF_PATH_MIXED;
+  thresholds[3] = !mixed ? 0 : (sd.Xhi && ws_supported(h->K) && !sd.heavy_tc) ? 1
+                             : (tc_supported(h->K) ? 2 : 0);
+  thresholds[4] = thresholds[3] == 1 ? sd.ws_cons : 0;
   return BPMF_OK;
 }
 

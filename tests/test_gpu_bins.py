@@ -122,7 +122,8 @@ def test_autotune_keeps_state_and_parity(gpu_lib, name):
         with pytest.raises(bp.BpmfError):
             s.sweep(0)
         for side in (0, 1):
-            tiny, light, hub = s.thresholds(side)
+            tiny, light, hub, heavy, cons = s.thresholds(side)
+            assert heavy in (1, 2) and cons >= 0
             assert -1 <= tiny <= light and hub >= 1
             bins, _ = s.sweep_info(side)
             assert bins.sum() == (ds.M if side == 0 else ds.N)
