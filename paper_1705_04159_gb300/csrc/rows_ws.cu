@@ -52,11 +52,17 @@ constexpr int kWsStageBytes = 2 * kWsOpBytes;  // hi + lo
 constexpr int kWsMaxStages = 16;
 constexpr int kWsMaxCons = 7;
 constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (see the gather loop)
-constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (4 floats of skew against bank conflicts)
+constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (see trow)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
 constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound per wait
 constexpr uint32_t kWsAccCols = 128;
+
+// Offset of row r in a tile: rows 0-3 at 8 r, rows 4-7 four floats further.
+// Tiles are 68 floats apart, so tile bases fall on eight different bank
+// groups, and the two halves of a tile (read by the two lanes that share
+// it in the trailing update) fall on different banks.
+__host__ __device__ __forceinline__ int trow(int r) { return r * 8 + ((r >> 2) << 2); }
 
 struct WsGeom {
   int K, KA, g, KP, NP, nfull, cb, ntile;
@@ -405,7 +411,7 @@ __device__ __forceinline__ void ws_fill_base(const SweepArgs& a, const WsGeom& G
         x[i] = (m < G.KA && n < G.KA) ? (n <= m ? __ldg(a.lamaug + m * G.KA + n) : 0.f)
                                       : (n == m ? 1.f : 0.f);
       }
-      st8(base + (I * (I + 1) / 2 + J) * kWsTileF + p * 8, x);
+      st8(base + (I * (I + 1) / 2 + J) * kWsTileF + trow(p), x);
     }
   }
 }
@@ -460,7 +466,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
           if (J <= I) {
             float x[8];
             float dv = 0.f;
-            const int toff = (I * (I + 1) / 2 + J) * kWsTileF + p * 8;
+            const int toff = (I * (I + 1) / 2 + J) * kWsTileF + trow(p);
             ld8(w.base + toff, x);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -499,7 +505,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
     float* D = T + tidx(p, p) * kWsTileF;
     float d[8][8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) ld8(D + i * 8, d[i]);
+    for (int i = 0; i < 8; ++i) ld8(D + trow(i), d[i]);
     float rdv[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -527,7 +533,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
     if (lane < 8) {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        if (lane == i) st8(D + i * 8, d[i]);
+        if (lane == i) st8(D + trow(i), d[i]);
       rinv[8 * p + lane] = lane == 0 ? rdv[0] : lane == 1 ? rdv[1] : lane == 2 ? rdv[2] :
                            lane == 3 ? rdv[3] : lane == 4 ? rdv[4] : lane == 5 ? rdv[5] :
                            lane == 6 ? rdv[6] : rdv[7];
@@ -536,7 +542,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
     const int nb = G.g - 1 - p;
     for (int rr = lane; rr < 8 * nb; rr += 32) {
       const int I = p + 1 + (rr >> 3);
-      float* row = T + tidx(I, p) * kWsTileF + (rr & 7) * 8;
+      float* row = T + tidx(I, p) * kWsTileF + trow(rr & 7);
       float x[8];
       ld8(row, x);
 #pragma unroll
@@ -560,11 +566,11 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
       while (i0 * (i0 + 1) / 2 > tt) --i0;
       const int I = p + 1 + i0, J = p + 1 + (tt - i0 * (i0 + 1) / 2);
       const float* LI = T + tidx(I, p) * kWsTileF;
-      const float* LJ = T + tidx(J, p) * kWsTileF + 32 * h;
+      const float* LJ = T + tidx(J, p) * kWsTileF + trow(4 * h);
       float* A = T + tidx(I, J) * kWsTileF + 4 * h;
       float lj[4][8];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) ld8(LJ + jj * 8, lj[jj]);
+      for (int jj = 0; jj < 4; ++jj) ld8(LJ + jj * 8, lj[jj]);  // rows 4h .. 4h + 3: contiguous
       float li[8];
       float4 ar;
       ld8(LI, li);
@@ -574,8 +580,8 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
         float lin[8];
         float4 arn = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ii < 7) {
-          ld8(LI + (ii + 1) * 8, lin);
-          arn = *reinterpret_cast<const float4*>(A + (ii + 1) * 8);
+          ld8(LI + trow(ii + 1), lin);
+          arn = *reinterpret_cast<const float4*>(A + trow(ii + 1));
         }
         float a4[4] = {ar.x, ar.y, ar.z, ar.w};
 #pragma unroll
@@ -585,7 +591,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
           for (int kk = 0; kk < 8; ++kk) s3 = fmaf(-li[kk], lj[jj][kk], s3);
           a4[jj] = s3;
         }
-        *reinterpret_cast<float4*>(A + ii * 8) = make_float4(a4[0], a4[1], a4[2], a4[3]);
+        *reinterpret_cast<float4*>(A + trow(ii)) = make_float4(a4[0], a4[1], a4[2], a4[3]);
         if (ii < 7) {
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) li[kk] = lin[kk];
@@ -630,7 +636,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
 #pragma unroll
       for (int mm = 0; mm < 4; ++mm) {
         const int i = lane + 32 * mm;
-        v[mm] = i < K ? T[tidx(IK, i >> 3) * kWsTileF + pk * 8 + (i & 7)] + zv[i] : 0.f;
+        v[mm] = i < K ? T[tidx(IK, i >> 3) * kWsTileF + trow(pk) + (i & 7)] + zv[i] : 0.f;
       }
       for (int I = (K - 1) >> 3; I >= 0; --I) {
         const int mI = I >> 2, l0 = (I & 3) * 8;  // rows 8I.. live in v[mI] of lanes l0..l0+7
@@ -647,7 +653,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
         for (int c = 7; c >= 0; --c) {
           float t2 = wb[c];
 #pragma unroll
-          for (int r2 = c + 1; r2 < 8; ++r2) t2 = fmaf(-Dg[r2 * 8 + c], u[r2], t2);
+          for (int r2 = c + 1; r2 < 8; ++r2) t2 = fmaf(-Dg[trow(r2) + c], u[r2], t2);
           u[c] = c < nI ? t2 * rinv[8 * I + c] : 0.f;
         }
         // the block's solution goes through shared memory (z of these rows
@@ -663,7 +669,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
             const float* Lc = T + tidx(I, i >> 3) * kWsTileF + (i & 7);
             float t2 = v[mm];
 #pragma unroll
-            for (int q2 = 0; q2 < 8; ++q2) t2 = fmaf(-Lc[q2 * 8], u[q2], t2);
+            for (int q2 = 0; q2 < 8; ++q2) t2 = fmaf(-Lc[trow(q2)], u[q2], t2);
             v[mm] = t2;
           }
         }
