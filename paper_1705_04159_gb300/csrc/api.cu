@@ -61,7 +61,7 @@ void free_handle(Handle* h) {
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
   dfree(h->flag_rows); dfree(h->flag_count); dfree(h->trow); dfree(h->tcol); dfree(h->tval);
   dfree(h->tsum); dfree(h->terr); dfree(h->hub_part); dfree(h->d_iter); dfree(h->d_navg);
-  dfree(h->ws_counter);
+  dfree(h->ws_counter); dfree(h->ws_base);
   delete h;
 }
 
@@ -344,6 +344,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     if ((rc = dalloc(&h->d_iter, 1))) break;
     if ((rc = dalloc(&h->d_navg, 1))) break;
     if ((rc = dalloc(&h->ws_counter, 1))) break;
+    if ((rc = dalloc(&h->ws_base, 136 * 68))) break;
     if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_iter, 0, sizeof(uint32_t), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->d_navg, 0, sizeof(int64_t), h->stream) != cudaSuccess) {

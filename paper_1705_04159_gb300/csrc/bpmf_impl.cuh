@@ -115,6 +115,7 @@ struct Handle {
   int64_t graph_kernels = 0;          // kernels per replay
 
   int* ws_counter = nullptr;  // row counter of the persistent row kernel
+  float* ws_base = nullptr;   // its base tiles (136 x 68 floats at most)
   // hub split partial Grams
   float* hub_part = nullptr;
   int64_t hub_part_len = 0;

@@ -366,6 +366,7 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.hub_piece0 = sd.hub_piece0;
   a.part = h->hub_part;
   a.work = sd.work;
+  a.wsbase = h->ws_base;
   a.Vhi = od.Xhi;
   a.Vlo = od.Xlo;
   a.KS = od.KS;

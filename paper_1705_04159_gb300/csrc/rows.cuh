@@ -39,6 +39,7 @@ struct SweepArgs {
   int KS;
   // per slot of the degree order: (row, first rating, one past the last, 0)
   const int4* work;
+  float* wsbase;        // base tiles of the persistent kernel (rows_ws.cu)
 };
 
 SweepArgs make_sweep_args(Handle* h, int s);

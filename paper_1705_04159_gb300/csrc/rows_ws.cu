@@ -93,7 +93,6 @@ struct RowRec {
 
 struct WsShared {
   uint8_t* stages;
-  float* base;   // bordered [[Lambda_s, b0], [b0^T, 0]] as lower 8 x 8 tiles, identity padding
   float* slots;
   uint64_t* full;
   uint64_t* empty;
@@ -117,16 +116,15 @@ __host__ __device__ inline int ws_fixed_bytes() {
   return 8 * (2 * kWsMaxStages + 4 + 2 * kWsMaxCons + 3) + 16 * kWsMaxStages + 16 * kWsRecs +
          4 * kWsMaxStages * kWsNb + 32;
 }
-// stages, base tiles, consumer slots, then the fixed part
+// stages, consumer slots, then the fixed part
 __host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C) {
-  return S * kWsStageBytes + G.ntile * kWsTileF * 4 + C * G.slot_floats() * 4 + ws_fixed_bytes();
+  return S * kWsStageBytes + C * G.slot_floats() * 4 + ws_fixed_bytes();
 }
 
 __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C) {
   WsShared w;
   w.stages = base;
-  w.base = reinterpret_cast<float*>(base + S * kWsStageBytes);
-  w.slots = w.base + G.ntile * kWsTileF;
+  w.slots = reinterpret_cast<float*>(base + S * kWsStageBytes);
   uint8_t* p = reinterpret_cast<uint8_t*>(w.slots + C * G.slot_floats());
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   w.full = b;
@@ -398,10 +396,13 @@ __device__ __forceinline__ void st8(float* p, const float (&x)[8]) {
   reinterpret_cast<float4*>(p)[1] = make_float4(x[4], x[5], x[6], x[7]);
 }
 
-// Base tiles: row m of tile (m / 8, J) for J <= m / 8, written once per launch
-// by the drain threads from the FP32 bordered hyper matrix.
-__device__ __forceinline__ void ws_fill_base(const SweepArgs& a, const WsGeom& G, float* base) {
-  for (int m = threadIdx.x - kWsGather; m < G.KP; m += kWsDrain) {
+// Base tiles (the bordered [[Lambda_s, b0], [b0^T, 0]] as lower 8 x 8 tiles,
+// identity on the padding): row m of tile (m / 8, J) for J <= m / 8, from the
+// FP32 bordered hyper matrix; one CTA writes them to global memory before
+// each launch of the row kernel, whose drain threads add alpha G to them.
+__global__ void ws_base_kernel(const SweepArgs a, float* base) {
+  const WsGeom G(a.K);
+  for (int m = threadIdx.x; m < G.KP; m += blockDim.x) {
     const int I = m >> 3, p = m & 7;
     for (int J = 0; J <= I; ++J) {
       float x[8];
@@ -414,6 +415,13 @@ __device__ __forceinline__ void ws_fill_base(const SweepArgs& a, const WsGeom& G
       st8(base + (I * (I + 1) / 2 + J) * kWsTileF + trow(p), x);
     }
   }
+}
+
+__device__ __forceinline__ void ldg8(const float* p, float (&x)[8]) {
+  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+  x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
 }
 
 // -------------------------------------------------------------- drain --
@@ -467,7 +475,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
             float x[8];
             float dv = 0.f;
             const int toff = (I * (I + 1) / 2 + J) * kWsTileF + trow(p);
-            ld8(w.base + toff, x);
+            ldg8(a.wsbase + toff, x);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int n = 8 * J + i;
@@ -720,7 +728,6 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
     tmem_alloc(w.taddr, 2 * kWsAccCols);
     tmem_relinquish();
   }
-  if (warp >= 4 && warp < 8) ws_fill_base(a, G, w.base);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -808,6 +815,9 @@ int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int* counter, int*
   const int smem = ws_smem_bytes(G, S, C);
   BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPMF_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  ws_base_kernel<<<1, 128, 0, st>>>(a, a.wsbase);
+  BPMF_CUDA_CHECK(cudaGetLastError());
+  if (launches) *launches += 1;
   const int grid = (int)std::min<int64_t>(num_sms, nrows);
   row_ws<<<grid, 32 * (kWsConsWarp0 + C), smem, st>>>(a, S, C, counter, status);
   BPMF_CUDA_CHECK(cudaGetLastError());
