@@ -515,12 +515,14 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
 #pragma unroll
     for (int i = 0; i < 8; ++i) ld8(D + trow(i), d[i]);
     float rdv[8];
+    float d0v[8];  // starting diagonals of the panel, off the pivot chain
+    ld8(diag0 + 8 * p, d0v);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int idx = 8 * p + c;
       float piv = d[c][c];
       if (idx < G.K) {
-        const float d0 = diag0[idx];
+        const float d0 = d0v[c];
         if (!(piv > kPivotRel * d0)) {
           fail = true;
           piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
