@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--autotune", type=int, default=1, choices=[0, 1])
     p.add_argument("--heavy", type=int, default=0, choices=[0, 1, 2],
                    help="heavy-row kernel: 0 tuned, 1 persistent, 2 one CTA per row")
+    p.add_argument("--thresholds", default=None,
+                   help="schedule for both sides instead of the autotuner's, as printed under "
+                        "bins.thresholds_tiny_light_hub: 'users;movies', five integers each, "
+                        "e.g. '-1,0,1099511627776,1,6;-1,0,1099511627776,1,2'")
     p.add_argument("--serving-jobs", type=int, default=256)
     p.add_argument("--serving-iters", type=int, default=50)
     p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],
@@ -206,7 +210,7 @@ def measured_peaks():
 
 # ------------------------------------------------------------- GPU arms --
 
-def device_arm(bp, ds, path, steps, warmup, world, stream, autotune=1, heavy=0):
+def device_arm(bp, ds, path, steps, warmup, world, stream, autotune=1, heavy=0, schedule=None):
     """Steady-state iterations with every input already in HBM."""
     import torch
     dev = torch.device("cuda")
@@ -217,6 +221,9 @@ def device_arm(bp, ds, path, steps, warmup, world, stream, autotune=1, heavy=0):
     s = bp.Sampler(ds.M, ds.N, t["train_row"], t["train_col"], t["train_val"], K=ds.K,
                    alpha=ds.alpha, seed=0, path=path, stream=stream, autotune=autotune,
                    heavy_kernel=heavy)
+    if schedule is not None:
+        for side in (0, 1):
+            s.set_thresholds(side, schedule[side])
     s.set_test(t["test_row"], t["test_col"], t["test_val"])
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
@@ -388,10 +395,15 @@ def main():
     K = ds.K
     work = algorithmic_work(ds, K)
     main_path = {"mixed": bp.PATH_MIXED, "binned": bp.PATH_BINNED, "plain": bp.PATH_PLAIN}[args.path]
+    schedule = None
+    if args.thresholds:
+        schedule = [tuple(int(x) for x in part.split(",")) for part in args.thresholds.split(";")]
+        if len(schedule) != 2 or any(len(t) != 5 for t in schedule):
+            raise SystemExit("--thresholds: 'users;movies', five integers each")
 
     with ClockSampler(local) as clk:
         mixed = device_arm(bp, ds, main_path, args.steps, args.warmup, world, stream,
-                           autotune=args.autotune, heavy=args.heavy)
+                           autotune=args.autotune, heavy=args.heavy, schedule=schedule)
     clocks = clk.summary()
     ms = max_over_ranks(world, mixed["ms"])
     rows = ds.M + ds.N
@@ -476,8 +488,9 @@ def main():
             "bins": {"users": mixed["info"][0][0].tolist(), "movies": mixed["info"][1][0].tolist(),
                      "fp64_rows": [mixed["info"][0][1], mixed["info"][1][1]],
                      "thresholds_tiny_light_hub": mixed["thresholds"],
-                     "autotune": "on: timed at the first init (init_s), reused from the "
-                                 "process cache by the e2e job"},
+                     "autotune": ("set by --thresholds" if schedule is not None else
+                                  "on: timed at the first init (init_s), reused from the "
+                                  "process cache by the e2e job" if args.autotune else "off")},
             "plain_fp32": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
             "serving": serving,
         }

@@ -214,6 +214,20 @@ BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *
  * Errors: EINVAL. */
 BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[5]);
 
+/* Sets the schedule of `side` from five values in bpmf_get_thresholds' order
+ * and meaning (host array, read only during the call), e.g. ones the
+ * autotuner chose in an earlier process: rows are re-binned by degree (the
+ * degree bins and hub splitting of paper Sec. IV-B) and the next step
+ * re-captures its graph.  tiny_max and light_max >= -1, hub_min >= 1; the
+ * kernel [3] must be one the path and K can run (what bpmf_get_thresholds
+ * could report: 1 or 2 on the MIXED path where supported, else 0), the
+ * consumer count [4] 0 (automatic) .. 16 with kernel 1 (more than fit in
+ * shared memory are cut to what fits), else 0.  On the PLAIN path only the
+ * values in effect are accepted.  Results are exact either way: the schedule
+ * changes which kernel draws a row, not the conditional it draws from.
+ * Errors: EINVAL (nothing changed), ECUDA. */
+BPMF_API int bpmf_set_thresholds(bpmf_t *h, int side, const int64_t thresholds[5]);
+
 /* ---- kernel timers (bpmf_get_timing) ---- */
 #define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */
 #define BPMF_T_HYPER_DRAW 1    /* FP64 Normal-Wishart draw */

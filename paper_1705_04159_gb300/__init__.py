@@ -20,7 +20,7 @@ __all__ = [
     "bpmf_sample_hyper", "bpmf_sweep", "bpmf_step", "bpmf_predict", "bpmf_test_rmse",
     "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
     "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
-    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds", "bpmf_set_thresholds",
     "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
     "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
     "Sampler", "Server", "Job", "JobResult", "TIMERS",
@@ -37,7 +37,7 @@ SYMBOLS = [
     "bpmf_step", "bpmf_predict", "bpmf_test_rmse", "bpmf_get_state", "bpmf_set_state",
     "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
     "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
-    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds",
+    "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds", "bpmf_set_thresholds",
     "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
     "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
 ]
@@ -123,6 +123,7 @@ def lib():
         L.bpmf_set_timing.argtypes = [P, C.c_int]
         L.bpmf_set_graph.argtypes = [P, C.c_int]
         L.bpmf_get_thresholds.argtypes = [P, C.c_int, P]
+        L.bpmf_set_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
         L.bpmf_hyper_stats_noalloc.argtypes = [P, i64, i32, P, P, P]
         L.bpmf_destroy.argtypes = [P]
@@ -323,6 +324,14 @@ def bpmf_get_thresholds(h, side):
     return tuple(int(x) for x in t)
 
 
+def bpmf_set_thresholds(h, side, thresholds):
+    """Applies five values in bpmf_get_thresholds' order to `side`."""
+    t = np.ascontiguousarray(thresholds, dtype=np.int64)
+    if t.shape != (5,):
+        raise ValueError("thresholds: five integers")
+    _check(lib().bpmf_set_thresholds(h, side, t.ctypes.data), "bpmf_set_thresholds")
+
+
 def bpmf_set_graph(h, enable=True):
     _check(lib().bpmf_set_graph(h, 1 if enable else 0), "bpmf_set_graph")
 
@@ -487,6 +496,9 @@ class Sampler:
 
     def thresholds(self, side):
         return bpmf_get_thresholds(self.h, side)
+
+    def set_thresholds(self, side, thresholds):
+        bpmf_set_thresholds(self.h, side, thresholds)
 
     def hyper(self):
         """(Lambda_U, mu_U, Lambda_V, mu_V) from the packed state."""

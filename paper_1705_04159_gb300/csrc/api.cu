@@ -662,6 +662,20 @@ int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[5]) {
   return BPMF_OK;
 }
 
+int bpmf_set_thresholds(bpmf_t* hh, int side, const int64_t thresholds[5]) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !valid_side(side) || !thresholds) return BPMF_EINVAL;
+  if (h->cfg.path == BPMF_PATH_PLAIN) {
+    // one kernel for every row: only the values in effect are accepted
+    int64_t cur[5];
+    bpmf_get_thresholds(hh, side, cur);
+    for (int i = 0; i < 5; ++i)
+      if (thresholds[i] != cur[i]) return BPMF_EINVAL;
+    return BPMF_OK;
+  }
+  return set_thresholds(h, side, thresholds);
+}
+
 int bpmf_get_sweep_info(bpmf_t* hh, int side, int64_t bins[4], int64_t* fp64_rows) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !valid_side(side)) return BPMF_EINVAL;

@@ -192,6 +192,26 @@ int setup_bins(Handle* h, int s) {
   return apply_bins(h, s, tiny, light, hub);
 }
 
+// Applies a schedule as bpmf_get_thresholds reports it (tiny_max, light_max,
+// hub_min, heavy-bin kernel, persistent-kernel consumers), e.g. one tuned in
+// an earlier process.  The kernel must be one this path and K can run.
+int set_thresholds(Handle* h, int s, const int64_t t[5]) {
+  SideDev& sd = h->side[s];
+  if (t[0] < -1 || t[1] < -1 || t[2] < 1 || t[4] < 0 || t[4] > 16) return BPMF_EINVAL;
+  const bool mixed = h->cfg.path == BPMF_PATH_MIXED;
+  const bool can_ws = mixed && sd.Xhi && ws_supported(h->K);
+  const bool can_tc = mixed && tc_supported(h->K);
+  const bool ok = t[3] == 1 ? can_ws : t[3] == 2 ? can_tc && t[4] == 0
+                : t[3] == 0 ? !can_ws && !can_tc && t[4] == 0 : false;
+  if (!ok) return BPMF_EINVAL;
+  const bool heavy_tc = t[3] == 2;
+  drop_graph(h);
+  BPMF_TRY(apply_bins(h, s, t[0], t[1], t[2]));
+  sd.heavy_tc = heavy_tc;
+  sd.ws_cons = (int)t[4];
+  return BPMF_OK;
+}
+
 // ---------------------------------------------------------------- autotune --
 // Each automatic threshold is chosen by timing one half-sweep of the side per
 // candidate (hyperparameters drawn from the initial factors, output written

@@ -227,6 +227,7 @@ int sort_test_set(Handle* h, const int32_t* d_row, const int32_t* d_col, const f
 int validate_pairs(Handle* h, const int32_t* d_row, const int32_t* d_col, int64_t n);
 int setup_bins(Handle* h, int s);
 int autotune_bins(Handle* h, int s, float* scratch);  // binned.cu
+int set_thresholds(Handle* h, int s, const int64_t t[5]);  // binned.cu
 
 // hyper.cu
 int launch_hyper(Handle* h, int s);

@@ -58,14 +58,17 @@ constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
 constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound per wait
 constexpr uint32_t kWsAccCols = 128;
 
+#include "ws_units.inc"
+
 // Offset of row r in a tile: rows 0-3 at 8 r, rows 4-7 four floats further.
-// Tiles are 68 floats apart, so tile bases fall on eight different bank
-// groups, and the two halves of a tile (read by the two lanes that share
-// it in the trailing update) fall on different banks.
+// Tiles are 68 floats apart, so consecutive tile bases fall on eight
+// different bank groups, and the two halves of a tile's rows on different
+// banks.  The trailing update's lane schedule (ws_units.inc, written by
+// gen_ws_units.py) is built for exactly this layout.
 __host__ __device__ __forceinline__ int trow(int r) { return r * 8 + ((r >> 2) << 2); }
 
 struct WsGeom {
-  int K, KA, g, KP, NP, nfull, cb, ntile;
+  int K, KA, g, KP, NP, nfull, cb, ntile, nround;
   __host__ __device__ explicit WsGeom(int K_) : K(K_) {
     KA = K + 1;
     g = (KA + 7) / 8;
@@ -74,9 +77,13 @@ struct WsGeom {
     nfull = K / 8;
     cb = K / 8;
     ntile = g * (g + 1) / 2;
+    nround = 0;  // rounds of 32 half-tile units over all panels (see ws_units.inc)
+    for (int nb = 1; nb < g; ++nb) nround += (nb * (nb + 1) + 31) / 32;
   }
   // consumer slot: header (4 ints), tiles, diag0, rinv, z
   __host__ __device__ int slot_floats() const { return 4 + ntile * kWsTileF + 3 * KP; }
+  // the trailing-update schedule of this g and its per-panel first rounds
+  __host__ __device__ int sched_bytes() const { return (64 * nround + 2 * (g + 1) + 15) & ~15; }
 };
 
 struct StageMeta {
@@ -94,6 +101,7 @@ struct RowRec {
 struct WsShared {
   uint8_t* stages;
   float* slots;
+  uint16_t* sched;  // [32 * nround] lane units, then [g + 1] first round of each panel
   uint64_t* full;
   uint64_t* empty;
   uint64_t* acc_full;
@@ -116,16 +124,17 @@ __host__ __device__ inline int ws_fixed_bytes() {
   return 8 * (2 * kWsMaxStages + 4 + 2 * kWsMaxCons + 3) + 16 * kWsMaxStages + 16 * kWsRecs +
          4 * kWsMaxStages * kWsNb + 32;
 }
-// stages, consumer slots, then the fixed part
+// stages, consumer slots, the trailing-update schedule, then the fixed part
 __host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C) {
-  return S * kWsStageBytes + C * G.slot_floats() * 4 + ws_fixed_bytes();
+  return S * kWsStageBytes + C * G.slot_floats() * 4 + G.sched_bytes() + ws_fixed_bytes();
 }
 
 __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C) {
   WsShared w;
   w.stages = base;
   w.slots = reinterpret_cast<float*>(base + S * kWsStageBytes);
-  uint8_t* p = reinterpret_cast<uint8_t*>(w.slots + C * G.slot_floats());
+  w.sched = reinterpret_cast<uint16_t*>(w.slots + C * G.slot_floats());
+  uint8_t* p = reinterpret_cast<uint8_t*>(w.sched) + G.sched_bytes();
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   w.full = b;
   w.empty = b + kWsMaxStages;
@@ -170,8 +179,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// 16-byte copy into shared memory through L2 only (.cg): the neighbour rows
+// have little reuse within one SM, and leaving L1 to the drain's base tiles
+// keeps those resident
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -505,8 +517,10 @@ __device__ __forceinline__ int tidx(int I, int J) { return I * (I + 1) / 2 + J; 
 // false if a pivot (of rows 0..K-1) fell below kPivotRel of its starting
 // diagonal; row K (the bordered right-hand side) and the padding rows are
 // never tested.
-__device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const float* diag0, float* rinv, int lane) {
+__device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const float* diag0, float* rinv,
+                                            const uint16_t* sched, int lane) {
   bool fail = false;
+  const uint16_t* sched_round = sched + 32 * G.nround;
   for (int p = 0; p < G.g; ++p) {
     // (a) diagonal tile, factored by every lane in registers (the same
     // values in all lanes: no shuffles), rows written back by lanes 0-7
@@ -566,15 +580,18 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
     }
     __syncwarp();
     // (c) trailing tiles (I, J), p < J <= I: A_IJ -= L_Ip L_Jp^T, in units
-    // of half a tile (4 of its 8 columns) so that more lanes have work; the
-    // rows of L_Ip and A_IJ are loaded one row ahead
-    const int ntl = nb * (nb + 1) / 2;
-    for (int u2 = lane; u2 < 2 * ntl; u2 += 32) {
-      const int tt = u2 >> 1, h = u2 & 1;
-      int i0 = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
-      while ((i0 + 1) * (i0 + 2) / 2 <= tt) ++i0;
-      while (i0 * (i0 + 1) / 2 > tt) --i0;
-      const int I = p + 1 + i0, J = p + 1 + (tt - i0 * (i0 + 1) / 2);
+    // of half a tile (4 of its 8 columns) so that more lanes have work, by
+    // the lane schedule of ws_units.inc (units grouped eight lanes at a time
+    // to keep their 128-bit accesses off each other's banks); the rows of
+    // L_Ip and A_IJ are loaded one row ahead
+    const int r0 = sched_round[p], r1 = sched_round[p + 1];
+    uint32_t e = r0 < r1 ? sched[32 * r0 + lane] : 0xFFFFu;
+    for (int r = r0; r < r1; ++r) {
+      const uint32_t e_next = r + 1 < r1 ? sched[32 * (r + 1) + lane] : 0xFFFFu;
+      const uint32_t ecur = e;
+      e = e_next;
+      if (ecur == 0xFFFFu) continue;
+      const int I = ecur & 15, J = (ecur >> 4) & 15, h = (ecur >> 8) & 1;
       const float* LI = T + tidx(I, p) * kWsTileF;
       const float* LJ = T + tidx(J, p) * kWsTileF + trow(4 * h);
       float* A = T + tidx(I, J) * kWsTileF + 4 * h;
@@ -635,7 +652,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
       if (4 * qd + 2 < K) zv[4 * qd + 2] = z.z;
       if (4 * qd + 3 < K) zv[4 * qd + 3] = z.w;
     }
-    const bool ok = ws_cholesky(G, T, diag0, rinv, lane);
+    const bool ok = ws_cholesky(G, T, diag0, rinv, w.sched, lane);
     if (ok) {
       // w = y + z with y = row K of L; u = L^-T w by 8-row blocks from the
       // bottom: every lane solves the block's 8 x 8 system against the
@@ -659,11 +676,12 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
         for (int q2 = 0; q2 < 8; ++q2) wb[q2] = __shfl_sync(0xffffffffu, own, l0 + q2);
         const float* Dg = T + tidx(I, I) * kWsTileF;
         const int nI = K - 8 * I < 8 ? K - 8 * I : 8;
+        // u[c] waits only for u[c + 1]: it enters the sum last
 #pragma unroll
         for (int c = 7; c >= 0; --c) {
           float t2 = wb[c];
 #pragma unroll
-          for (int r2 = c + 1; r2 < 8; ++r2) t2 = fmaf(-Dg[trow(r2) + c], u[r2], t2);
+          for (int r2 = 7; r2 > c; --r2) t2 = fmaf(-Dg[trow(r2) + c], u[r2], t2);
           u[c] = c < nI ? t2 * rinv[8 * I + c] : 0.f;
         }
         // the block's solution goes through shared memory (z of these rows
@@ -679,7 +697,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
             const float* Lc = T + tidx(I, i >> 3) * kWsTileF + (i & 7);
             float t2 = v[mm];
 #pragma unroll
-            for (int q2 = 0; q2 < 8; ++q2) t2 = fmaf(-Lc[trow(q2)], u[q2], t2);
+            for (int q2 = 7; q2 >= 0; --q2) t2 = fmaf(-Lc[trow(q2)], u[q2], t2);
             v[mm] = t2;
           }
         }
@@ -726,6 +744,12 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
   // operand chunks past the last written one (features beyond K) stay zero
   for (int e = threadIdx.x; e < S * kWsStageBytes / 16; e += blockDim.x)
     reinterpret_cast<uint4*>(w.stages)[e] = make_uint4(0, 0, 0, 0);
+  {  // this g's trailing-update schedule, rounds counted from its first
+    const unsigned short* rr = kWsUnitRound[G.g - kWsUnitGMin];
+    const int r0 = rr[0];
+    for (int e = threadIdx.x; e < 32 * G.nround; e += blockDim.x) w.sched[e] = kWsUnits[32 * r0 + e];
+    for (int e = threadIdx.x; e <= G.g; e += blockDim.x) w.sched[32 * G.nround + e] = (uint16_t)(rr[e] - r0);
+  }
   if (warp == kWsMmaWarp) {
     tmem_alloc(w.taddr, 2 * kWsAccCols);
     tmem_relinquish();
@@ -770,7 +794,10 @@ __global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, in
 
 }  // namespace
 
-bool ws_supported(int K) { return K >= 8 && K + 1 <= 128; }
+bool ws_supported(int K) {
+  const int g = (K + 8) / 8;  // tiles per side of the bordered matrix
+  return K >= 8 && K + 1 <= 128 && g >= kWsUnitGMin && g <= kWsUnitGMax;
+}
 
 // Stages (a multiple of 4, one or more ring slots per gather warp) and
 // consumer warps for latent dimension K.  With `cons` > 0 that many

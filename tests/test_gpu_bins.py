@@ -134,3 +134,39 @@ def test_autotune_keeps_state_and_parity(gpu_lib, name):
             got = s.get_state()[side]
             ref = oracle_sweep(ds, side, U, V, hy, ds.alpha, 31, 1, structure=st)
             assert rel_err(got, ref).max() <= 1e-3
+
+
+def test_set_thresholds_reproduces_a_tuned_schedule(gpu_lib):
+    """The schedule an autotuned sampler chose, applied to an untuned one,
+    gives the same bins and bitwise the same draws; values no kernel of the
+    path can run are refused and change nothing."""
+    bp = gpu_lib
+    ds, K, _ = _case("powerlaw_k100")
+    U, V, _, hyper = random_state(ds, K)
+    with _sampler(bp, ds, K, bp.PATH_MIXED, seed=37, autotune=1) as tuned, \
+            _sampler(bp, ds, K, bp.PATH_MIXED, seed=37) as plain:
+        outs = []
+        for side in (0, 1):
+            t = tuned.thresholds(side)
+            plain.set_thresholds(side, t)
+            assert plain.thresholds(side) == t
+            assert np.array_equal(plain.sweep_info(side)[0], tuned.sweep_info(side)[0])
+        for s in (tuned, plain):
+            s.set_state(U, V, hyper, it=3)
+            s.sweep(0)
+            s.sweep(1)
+            outs.append(s.get_state()[:2])
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        before = plain.thresholds(0)
+        for bad in ((-2, 0, 8192, 1, 0), (0, 0, 0, 1, 0), (0, 0, 8192, 0, 0), (0, 0, 8192, 2, 3),
+                    (0, 0, 8192, 1, 17)):
+            with pytest.raises(bp.BpmfError):
+                plain.set_thresholds(0, bad)
+            assert plain.thresholds(0) == before
+        # the other heavy-row kernel on the same bins: the same draws to the
+        # tolerance of the tensor-core Gram
+        plain.set_thresholds(0, (before[0], before[1], before[2], 2, 0))
+        assert plain.thresholds(0)[3] == 2
+        plain.set_state(U, V, hyper, it=3)
+        plain.sweep(0)
+        assert rel_err(plain.get_state()[0], outs[0][0]).max() <= 1e-3
