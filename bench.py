@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--thresholds", default=None,
                    help="schedule for both sides instead of the autotuner's, as printed under "
                         "bins.thresholds_tiny_light_hub: 'users;movies', five integers each, "
-                        "e.g. '-1,0,1099511627776,1,6;-1,0,1099511627776,1,2'")
+                        "e.g. --thresholds=-1,0,1099511627776,1,6;-1,0,1099511627776,1,2")
     p.add_argument("--serving-jobs", type=int, default=256)
     p.add_argument("--serving-iters", type=int, default=50)
     p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],

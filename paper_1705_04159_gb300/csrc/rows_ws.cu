@@ -523,7 +523,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
   const uint16_t* sched_round = sched + 32 * G.nround;
   for (int p = 0; p < G.g; ++p) {
     // (a) diagonal tile, factored by every lane in registers (the same
-    // values in all lanes: no shuffles), rows written back by lanes 0-7
+    // values in all lanes: no shuffles)
     float* D = T + tidx(p, p) * kWsTileF;
     float d[8][8];
 #pragma unroll
@@ -535,14 +535,13 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
     for (int c = 0; c < 8; ++c) {
       const int idx = 8 * p + c;
       float piv = d[c][c];
-      if (idx < G.K) {
+      {  // without branches: the lanes stay converged through the chain
         const float d0 = d0v[c];
-        if (!(piv > kPivotRel * d0)) {
-          fail = true;
-          piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
-        }
-      } else {
-        piv = fmaxf(piv, FLT_MIN);  // row K (never used as a pivot) or padding (1)
+        const bool real = idx < G.K;  // row K (never a pivot) and padding rows are not tested
+        const bool bad = real && !(piv > kPivotRel * d0);
+        fail = fail || bad;
+        const float fix = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+        piv = bad ? fix : (real ? piv : fmaxf(piv, FLT_MIN));
       }
       const float rd = rsqrtf(piv);
       rdv[c] = rd;
@@ -554,14 +553,11 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
 #pragma unroll
         for (int i = j2; i < 8; ++i) d[i][j2] = fmaf(-d[i][c], d[j2][c], d[i][j2]);
     }
-    if (lane < 8) {
+    // every lane holds the same factor, so every lane writes it: same
+    // address, same value, no divergent stores
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (lane == i) st8(D + trow(i), d[i]);
-      rinv[8 * p + lane] = lane == 0 ? rdv[0] : lane == 1 ? rdv[1] : lane == 2 ? rdv[2] :
-                           lane == 3 ? rdv[3] : lane == 4 ? rdv[4] : lane == 5 ? rdv[5] :
-                           lane == 6 ? rdv[6] : rdv[7];
-    }
+    for (int i = 0; i < 8; ++i) st8(D + trow(i), d[i]);
+    st8(rinv + 8 * p, rdv);
     // (b) panel rows below: x L_pp^T = a, row by row, against the registers
     const int nb = G.g - 1 - p;
     for (int rr = lane; rr < 8 * nb; rr += 32) {
