@@ -326,7 +326,7 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     // stage ring (rows with many ratings), more factor more rows at once
     int best_c = 0;
     float best = 3.0e38f;
-    for (int c : {0, 2, 3, 4, 5, 6}) {
+    for (int c : {0, 1, 2, 3, 4, 5, 6}) {
       sd.ws_cons = c;
       if (time_sweep(h, s, scratch, reps, &ms) != BPMF_OK) {
         cudaGetLastError();  // that many consumers do not fit: not a candidate

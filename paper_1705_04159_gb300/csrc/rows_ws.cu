@@ -265,12 +265,14 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   const int t = threadIdx.x;
   const int wg = t >> 5, lane = t & 31, k = lane;
   const int nrows = (int)(a.row_end - a.row_begin);
-  // with eight or more stages (two or more slots per warp) a warp keeps two
-  // of its stages in flight
-  const bool lag1 = S >= 8;
+  // a warp owns S / 4 ring slots and keeps that many of its stages in flight
+  // (up to four): the copies of the oldest are waited for only when a newer
+  // one has been issued
+  const int lag = S / 4 - 1 < 3 ? S / 4 - 1 : 3;
   uint32_t n = 0;             // stage sequence number (the same in every gather warp)
   int q = 0;                  // row sequence number
-  uint32_t pend = 0xffffffffu;  // this warp's issued stage not yet signalled
+  uint32_t pend[3] = {0u, 0u, 0u};  // this warp's issued stages not yet signalled, oldest first
+  int npend = 0;
   // thread 0 prefetches the next row's work entry (row, first, last rating)
   int4 wk = make_int4(-1, 0, 0, 0);
   int next_slot = 0;
@@ -334,15 +336,26 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
       if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, j, lane);
       w.rating[s * kWsNb + k] = k < cnt ? r : 0.f;
       cp_async_commit();
-      if (lag1) {
-        if (pend != 0xffffffffu) {
-          cp_async_wait<1>();
-          ws_signal(G, w, S, pend, lane);
+      if (npend == lag) {
+        // the oldest of lag + 1 outstanding copy groups has landed once at
+        // most lag remain
+        if (lag == 0) cp_async_wait<0>();
+        else if (lag == 1) cp_async_wait<1>();
+        else if (lag == 2) cp_async_wait<2>();
+        else cp_async_wait<3>();
+        if (lag == 0) {
+          ws_signal(G, w, S, nn, lane);
+        } else {
+          ws_signal(G, w, S, pend[0], lane);
+          pend[0] = lag > 1 ? pend[1] : nn;
+          pend[1] = lag > 2 ? pend[2] : nn;
+          pend[2] = nn;
         }
-        pend = nn;
       } else {
-        cp_async_wait<0>();
-        ws_signal(G, w, S, nn, lane);
+        pend[0] = npend == 0 ? nn : pend[0];
+        pend[1] = npend == 1 ? nn : pend[1];
+        pend[2] = npend == 2 ? nn : pend[2];
+        ++npend;
       }
     }
     n += (uint32_t)nst;
@@ -350,7 +363,9 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
     ++q;
   }
   cp_async_wait<0>();
-  if (pend != 0xffffffffu) ws_signal(G, w, S, pend, lane);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (i < npend) ws_signal(G, w, S, pend[i], lane);
 }
 
 // ---------------------------------------------------------------- MMA --
@@ -797,7 +812,7 @@ bool ws_supported(int K) {
 
 // Stages (a multiple of 4, one or more ring slots per gather warp) and
 // consumer warps for latent dimension K.  With `cons` > 0 that many
-// consumers (if they fit) and the deepest ring up to 8 stages that fits;
+// consumers (if they fit) and the deepest ring up to 16 stages that fits;
 // otherwise 8 stages if at least 3 consumers fit beside them, else 4 stages
 // and as many consumers as fit.
 int ws_config(int K, int cons, int* S, int* C) {
@@ -816,7 +831,8 @@ int ws_config(int K, int cons, int* S, int* C) {
   int s = 8, c = 0;
   if (cons > 0) {
     c = std::min(cons, kWsMaxCons);
-    if (ws_smem_bytes(G, s, c) > max_smem) s = 4;
+    s = 16;
+    while (s > 4 && ws_smem_bytes(G, s, c) > max_smem) s -= 4;
   } else {
     c = fit_cons(s);
     if (c < 3) {

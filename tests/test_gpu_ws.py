@@ -80,3 +80,29 @@ def test_persistent_rows_chain_is_deterministic(gpu_lib):
                 s.step()
             outs.append(s.get_state()[:2])
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("name,cons", [("wide_k100", 1), ("wide_k100", 2), ("wide_k100", 6),
+                                       ("k8", 1), ("k33", 2), ("k127", 1)])
+def test_consumer_counts_and_ring_depths(gpu_lib, name, cons):
+    """Fewer consumer warps leave room for a deeper stage ring (a gather warp
+    then keeps up to four of its stages in flight); every such
+    configuration draws the same rows, bitwise, as the automatic one."""
+    bp = gpu_lib
+    ds, K, st = _case(name)
+    U, V, hy, hyper = random_state(ds, K)
+    outs = []
+    for c in (0, cons):
+        with bp.Sampler(ds.M, ds.N, ds.train_row, ds.train_col, ds.train_val, K=K, alpha=ds.alpha,
+                        seed=13, path=bp.PATH_MIXED, heavy_kernel=1, tiny_max=-1) as s:
+            for side in (0, 1):
+                t = list(s.thresholds(side))
+                s.set_thresholds(side, t[:4] + [c])
+                assert s.thresholds(side)[4] == c
+            s.set_state(U, V, hyper, it=4)
+            s.sweep(0)
+            s.sweep(1)
+            outs.append(s.get_state()[:2])
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref = oracle_sweep(ds, 0, U, V, hy, ds.alpha, 13, 4, structure=st)
+    assert rel_err(outs[1][0], ref).max() <= 1e-3
