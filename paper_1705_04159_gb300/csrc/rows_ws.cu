@@ -55,7 +55,8 @@ constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (se
 constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (see trow)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
-constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound per wait
+constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound (final MMA wait)
+constexpr uint64_t kWsWaitNs = 2000000000ull;  // 2 s bound per pipeline wait
 constexpr uint32_t kWsAccCols = 128;
 
 #include "ws_units.inc"
@@ -156,12 +157,25 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   return w;
 }
 
-// Bounded wait by one thread: gives up (setting abort) after kWsPolls
-// suspending polls, or as soon as another role has aborted.
+__device__ __forceinline__ uint64_t ws_gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait by one thread: polls without a suspend hint (a suspended
+// thread resumes late, and every hand-off of the pipeline pays for it), and
+// gives up (setting abort) after kWsWaitNs of wall-clock time, or as soon as
+// another role has aborted.
 __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  for (uint32_t i = 0; i < kWsPolls; ++i) {
-    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-    if (*abort) return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = ws_gtimer();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 31u) == 0u) {
+      if (*abort) return false;
+      if (ws_gtimer() - t0 > kWsWaitNs) break;
+    }
   }
   *abort = 1;
   return false;
