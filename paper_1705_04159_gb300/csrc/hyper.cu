@@ -142,19 +142,25 @@ __global__ void scatter_final(const double* __restrict__ part, int blocks, int K
 
 // In-place lower Cholesky (upper part zeroed).  Returns false (to all
 // threads) if a pivot is not positive.
+// FP64 square roots and divisions are many FP64 instructions each, so the
+// pivot's root and reciprocal are taken once, by thread 0, and the column is
+// scaled by the reciprocal.
 __device__ bool cta_cholesky(double* A, int K, int* bad) {
+  __shared__ double s_rd;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) *bad = 0;
   __syncthreads();
   for (int k = 0; k < K; ++k) {
-    const double piv = A[k * K + k];
-    const double d = piv > 0.0 ? sqrt(piv) : 1.0;
-    __syncthreads();
-    if (!(piv > 0.0)) {
-      if (tid == 0) *bad = 1;
+    if (tid == 0) {
+      const double piv = A[k * K + k];
+      const double d = piv > 0.0 ? sqrt(piv) : 1.0;
+      if (!(piv > 0.0)) *bad = 1;
+      A[k * K + k] = d;
+      s_rd = 1.0 / d;
     }
-    for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] /= d;
-    if (tid == 0) A[k * K + k] = d;
+    __syncthreads();
+    const double rd = s_rd;
+    for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] *= rd;
     __syncthreads();
     const int m = K - k - 1;
     for (int e = tid; e < m * m; e += nt) {
@@ -173,17 +179,34 @@ __device__ bool cta_cholesky(double* A, int K, int* bad) {
   return ok;
 }
 
+// Four-way split sum of p[k] q[k] (strides sp, sq) over k = 0 .. n-1: four
+// independent chains instead of one.
+__device__ __forceinline__ double dot4(const double* p, int sp, const double* q, int sq, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+    s0 = fma(p[k * sp], q[k * sq], s0);
+    s1 = fma(p[(k + 1) * sp], q[(k + 1) * sq], s1);
+    s2 = fma(p[(k + 2) * sp], q[(k + 2) * sq], s2);
+    s3 = fma(p[(k + 3) * sp], q[(k + 3) * sq], s3);
+  }
+  for (; k < n; ++k) s0 = fma(p[k * sp], q[k * sq], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
 // Linv = L^-1 for lower-triangular L: thread j solves column j by forward
 // substitution.
 __device__ void cta_tri_inverse(const double* L, double* Linv, int K) {
+  __shared__ double rdiag[kMaxK];  // 1 / L_ii, one division per row
+  for (int i = threadIdx.x; i < K; i += blockDim.x) rdiag[i] = 1.0 / L[i * K + i];
+  __syncthreads();
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
     for (int i = 0; i < K; ++i) {
       double v;
       if (i < j) v = 0.0;
       else {
-        double t = (i == j) ? 1.0 : 0.0;
-        for (int k = j; k < i; ++k) t -= L[i * K + k] * Linv[k * K + j];
-        v = t / L[i * K + i];
+        const double t = (i == j ? 1.0 : 0.0) - dot4(L + i * K + j, 1, Linv + j * K + j, K, i - j);
+        v = t * rdiag[i];
       }
       Linv[i * K + j] = v;
     }
@@ -292,15 +315,21 @@ struct HyperArgs {
 //    (lower triangular with a positive diagonal, hence the Cholesky factor);
 //  * chol(beta* Lambda) = sqrt(beta*) B for B = C A (lower triangular with a
 //    positive diagonal and Lambda = B B^T), so mu = mu* + B^-T z / sqrt(beta*).
-__global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
+// The steps with a chain through K (Cholesky, inverse, Bartlett draws, the
+// back substitution for mu) run in one CTA; B = C A and Lambda = B B^T, each
+// K^3 / 6 multiply-adds with no chain between rows, run one CTA per row.
+// Scratch (doubles): Mx | T | A | B (K*K each) | mu* | x (K each) | ...;
+// scr[5 K*K] = 1 once the factorisation succeeded (0: the later steps skip).
+
+// (3a) posterior, L_M, T = L_M^-1, Bartlett A and mu*, by one CTA
+__global__ void __launch_bounds__(512) wishart_factor(HyperArgs a) {
   __shared__ int bad;
   const int K = a.K, KK = K * K;
   double* Mx = a.scr;          // J W*^-1 J, then its Cholesky factor L_M
   double* T = Mx + KK;         // L_M^-1
   double* A = T + KK;          // Bartlett A
-  double* B = A + KK;          // C A
-  double* mus = B + KK;        // mu*
-  double* x = mus + K;         // solve workspace
+  double* mus = A + 2 * KK;    // mu*
+  double* ok = a.scr + 5 * KK;
   const double n = (double)a.n;
   const double w = a.beta0 * n / (a.beta0 + n);
   for (int e = threadIdx.x; e < KK; e += blockDim.x) {
@@ -310,47 +339,74 @@ __global__ void __launch_bounds__(512) wishart_draw(HyperArgs a) {
   for (int k = threadIdx.x; k < K; k += blockDim.x)
     mus[k] = (a.beta0 * a.mu0[k] + n * a.xbar[k]) / (a.beta0 + n);
   __syncthreads();
-  const double beta_s = a.beta0 + n, nu_s = a.nu0 + n;
+  const double nu_s = a.nu0 + n;
   if (!cta_cholesky(Mx, K, &bad)) {
-    if (threadIdx.x == 0) atomicOr(a.status, kStatusNotPD);
+    if (threadIdx.x == 0) {
+      *ok = 0.0;
+      atomicOr(a.status, kStatusNotPD);
+    }
     return;
   }
   cta_tri_inverse(Mx, T, K);
-  const uint2 key = seed_key(a.seed);
-  const uint32_t t = *a.tp;
-  cta_bartlett_A(A, K, nu_s, key, t, a.side, a.status);
-  // B = C A on the lower triangle, C[i][m] = T[K-1-m][K-1-i]
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
-    const int i = e / K, j = e % K;
-    double v = 0.0;
-    if (j <= i)
-      for (int m = j; m <= i; ++m) v += T[(K - 1 - m) * K + (K - 1 - i)] * A[m * K + j];
-    B[e] = v;
-    // Lambda = B B^T with B lower, positive diagonal: B = chol(Lambda), packed by rows
+  cta_bartlett_A(A, K, nu_s, seed_key(a.seed), *a.tp, a.side, a.status);
+  if (threadIdx.x == 0) *ok = 1.0;
+}
+
+// (3b) row i of B = C A (blockIdx.x = i), and its FP32 copy packed by rows:
+// B = chol(Lambda) for the rank-one row kernel
+__global__ void __launch_bounds__(128) wishart_b(HyperArgs a) {
+  const int K = a.K, KK = K * K, i = blockIdx.x;
+  if (a.scr[5 * KK] == 0.0) return;
+  const double* T = a.scr + KK;
+  const double* A = T + KK;
+  double* B = a.scr + 3 * KK;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    // B[i][j] = sum over m = j .. i of C[i][m] A[m][j], C[i][m] = T[K-1-m][K-1-i]
+    const double v = j <= i ? dot4(T + (K - 1 - j) * K + (K - 1 - i), -K, A + j * K + j, K, i - j + 1)
+                            : 0.0;
+    B[i * K + j] = v;
     if (j <= i) a.lchol[i * (i + 1) / 2 + j] = (float)v;
   }
-  __syncthreads();
-  // Lambda = B B^T (lower triangle, mirrored)
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
-    const int i = e / K, j = e % K;
-    if (j > i) continue;
-    double v = 0.0;
-    for (int m = 0; m <= j; ++m) v += B[i * K + m] * B[j * K + m];
+}
+
+// (3c) row i of Lambda = B B^T (lower triangle, mirrored)
+__global__ void __launch_bounds__(128) wishart_lam(HyperArgs a) {
+  const int K = a.K, KK = K * K, i = blockIdx.x;
+  if (a.scr[5 * KK] == 0.0) return;
+  const double* B = a.scr + 3 * KK;
+  for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+    const double v = dot4(B + i * K, 1, B + j * K, 1, j + 1);
     a.lam[i * K + j] = v;
     a.lam[j * K + i] = v;
   }
-  __syncthreads();
-  // mu = mu* + B^-T z / sqrt(beta*), back substitution by one thread
-  if (threadIdx.x == 0) {
-    const uint32_t sw = stream_word(kStreamHyperMu, a.side);
-    for (int i = K - 1; i >= 0; --i) {
-      double v = (double)normal_at_f32(key, 0u, t, sw, (uint32_t)i);
-      for (int k = i + 1; k < K; ++k) v -= B[k * K + i] * x[k];
-      x[i] = v / B[i * K + i];
-    }
-    const double rb = 1.0 / sqrt(beta_s);
-    for (int i = 0; i < K; ++i) a.mu[i] = mus[i] + x[i] * rb;
+}
+
+// (3d) mu = mu* + B^-T z / sqrt(beta*) by one CTA: back substitution from the
+// bottom, each solved x_i subtracted from the remaining right-hand sides by
+// all threads; then the FP32 bordered copy
+__global__ void __launch_bounds__(128) wishart_mu(HyperArgs a) {
+  __shared__ double xs[kMaxK], zr[kMaxK], rd[kMaxK];
+  const int K = a.K, KK = K * K;
+  if (a.scr[5 * KK] == 0.0) return;
+  const double* B = a.scr + 3 * KK;
+  const double* mus = a.scr + 4 * KK;
+  const uint2 key = seed_key(a.seed);
+  const uint32_t t = *a.tp;
+  const uint32_t sw = stream_word(kStreamHyperMu, a.side);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    zr[k] = (double)normal_at_f32(key, 0u, t, sw, (uint32_t)k);
+    rd[k] = 1.0 / B[k * K + k];
   }
+  __syncthreads();
+  for (int i = K - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) xs[i] = zr[i] * rd[i];
+    __syncthreads();
+    const double xi = xs[i];
+    for (int k = threadIdx.x; k < i; k += blockDim.x) zr[k] = fma(-B[i * K + k], xi, zr[k]);
+    __syncthreads();
+  }
+  const double rb = 1.0 / sqrt(a.beta0 + (double)a.n);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) a.mu[k] = mus[k] + xs[k] * rb;
   __syncthreads();
   write_bordered(a.lam, a.mu, K, a.lamaug);
 }
@@ -445,9 +501,12 @@ int launch_hyper(Handle* h, int s) {
   a.status = h->status;
   {
     PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
-    wishart_draw<<<1, 512, 0, st>>>(a);
+    wishart_factor<<<1, 512, 0, st>>>(a);
+    wishart_b<<<K, 128, 0, st>>>(a);
+    wishart_lam<<<K, 128, 0, st>>>(a);
+    wishart_mu<<<1, 128, 0, st>>>(a);
     BPMF_CUDA_CHECK(cudaGetLastError());
-    h->kernels += 1;
+    h->kernels += 4;
   }
   sd.have_hyper = true;
   sd.have_stats = true;
