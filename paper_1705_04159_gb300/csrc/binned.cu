@@ -52,7 +52,7 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
     r.row_begin = e_hub;
     r.row_end = e_heavy;
     if (sd.Xhi && ws_supported(h->K) && !sd.heavy_tc)
-      BPMF_TRY(launch_rows_ws(r, h->num_sms, sd.ws_cons, h->ws_counter, h->status, st,
+      BPMF_TRY(launch_rows_ws(r, h->num_sms, sd.ws_cons, sd.ws_nb, h->ws_counter, h->status, st,
                               &h->kernels));
     else if (tc)
       BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
@@ -186,6 +186,7 @@ int setup_bins(Handle* h, int s) {
   BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
   sd.hub_min = 0;  // forces the pieces to be built
   sd.heavy_tc = h->cfg.heavy_kernel == 2 && tc_supported(h->K);
+  sd.ws_nb = ws_stage_neighbours(R > 0 ? sd.ptr_h[R] : 0, R);
   const int64_t tiny = h->cfg.tiny_max >= 0 ? h->cfg.tiny_max : default_tiny_max(h);
   const int64_t light = h->cfg.light_max >= 0 ? h->cfg.light_max : tiny;
   const int64_t hub = h->cfg.hub_min >= 0 ? h->cfg.hub_min : 2 * kPiece;

@@ -58,9 +58,11 @@ int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStrea
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 // heavy rows by the persistent warp-specialised kernel (rows_ws.cu)
 bool ws_supported(int K);
-// cons: consumer warps per CTA (0: automatic)
-int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int* counter, int* status,
+// cons: consumer warps per CTA (0: automatic); nb: neighbours per stage (32 or 64)
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* counter, int* status,
                    cudaStream_t st, int64_t* launches);
+// neighbours per stage of the persistent kernel for a side with nnz ratings over R rows
+int ws_stage_neighbours(int64_t nnz, int64_t R);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
 int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
 

@@ -44,11 +44,17 @@
 namespace gb {
 namespace {
 
-constexpr int kWsNb = 32;            // neighbours per stage (two MMA K-steps)
 constexpr int kWsLBO = 128;          // operand tiles: bytes between 8-neighbour groups
-constexpr int kWsSBO = kWsNb * 16;   //   and between 8-feature chunks
-constexpr int kWsOpBytes = 16 * kWsSBO;        // 128 features (the MMA reads M = 128 rows)
-constexpr int kWsStageBytes = 2 * kWsOpBytes;  // hi + lo
+constexpr int64_t kWsLongRow = 256;  // mean ratings per row from which stages hold 64 neighbours
+// Neighbours per stage NB: 32 (two MMA K-steps) or 64 (four), chosen per side:
+// bigger stages halve the hand-offs per neighbour where rows are long.
+template <int NB>
+struct WsNb {
+  static constexpr int kSBO = NB * 16;              // bytes between 8-feature chunks
+  static constexpr int kOpBytes = 16 * kSBO;        // 128 features (the MMA reads M = 128 rows)
+  static constexpr int kStageBytes = 2 * kOpBytes;  // hi + lo
+};
+__host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 16 * nb * 16; }
 constexpr int kWsMaxStages = 16;
 constexpr int kWsMaxCons = 7;
 constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (see the gather loop)
@@ -120,20 +126,20 @@ struct WsShared {
   uint32_t* taddr;
 };
 
-__host__ __device__ inline int ws_fixed_bytes() {
+__host__ __device__ inline int ws_fixed_bytes(int nb) {
   // barriers (2 S + 4 + 2 C + 3), stage meta, row records, ratings, next_row, abort, taddr
   return 8 * (2 * kWsMaxStages + 4 + 2 * kWsMaxCons + 3) + 16 * kWsMaxStages + 16 * kWsRecs +
-         4 * kWsMaxStages * kWsNb + 32;
+         4 * kWsMaxStages * nb + 32;
 }
 // stages, consumer slots, the trailing-update schedule, then the fixed part
-__host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C) {
-  return S * kWsStageBytes + C * G.slot_floats() * 4 + G.sched_bytes() + ws_fixed_bytes();
+__host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C, int nb) {
+  return S * ws_stage_bytes(nb) + C * G.slot_floats() * 4 + G.sched_bytes() + ws_fixed_bytes(nb);
 }
 
-__device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C) {
+__device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C, int nb) {
   WsShared w;
   w.stages = base;
-  w.slots = reinterpret_cast<float*>(base + S * kWsStageBytes);
+  w.slots = reinterpret_cast<float*>(base + S * ws_stage_bytes(nb));
   w.sched = reinterpret_cast<uint16_t*>(w.slots + C * G.slot_floats());
   uint8_t* p = reinterpret_cast<uint8_t*>(w.sched) + G.sched_bytes();
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
@@ -150,7 +156,7 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   w.meta = reinterpret_cast<StageMeta*>(p);
   w.recs = reinterpret_cast<RowRec*>(p + 16 * kWsMaxStages);
   w.rating = reinterpret_cast<float*>(p + 16 * kWsMaxStages + 16 * kWsRecs);
-  int* q = reinterpret_cast<int*>(w.rating + kWsMaxStages * kWsNb);
+  int* q = reinterpret_cast<int*>(w.rating + kWsMaxStages * nb);
   w.next_row = q;
   w.abort = q + 4;
   w.taddr = reinterpret_cast<uint32_t*>(q + 5);
@@ -218,41 +224,41 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
 // ------------------------------------------------------------- gather --
 // The four gather warps take the stages of the row sequence in turn (stage n
 // by warp n % 4), so four stages are filled side by side.  In the warp that
-// fills stage n, lane l handles neighbour l and every chunk c of it, so the
-// warp writes chunk c of all 32 neighbours as 512 contiguous bytes.  Chunks 0 ..
-// ceil(K/8) - 1 are 16-byte copies of the shadow row (its padding past K is
-// zero); the rating (feature K, in chunk cb = K / 8) is patched in once the
-// copy of its chunk has landed (ws_patch_rating).  Rows k >= cnt are zeroed.
+// fills stage n, lane l handles neighbours l, l + 32, .. (NB / 32 of them) and
+// every chunk c of each, so the warp writes chunk c of 32 neighbours as 512
+// contiguous bytes.  Chunks 0 .. ceil(K/8) - 1 are 16-byte copies of the
+// shadow row (its padding past K is zero); the rating (feature K, in chunk
+// cb = K / 8) is patched in once the copy of its chunk has landed
+// (ws_patch_rating).  Rows k >= cnt are zeroed.
+template <int NB>
 __device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs& a,
-                                                uint8_t* stage, int cnt, int32_t j, int lane) {
-  const int k = lane;
+                                                uint8_t* stage, int cnt, int32_t j, int k) {
   const bool live = k < cnt;
   const __nv_bfloat16* hrow = a.Vhi + (int64_t)j * a.KS;
   const __nv_bfloat16* lrow = a.Vlo + (int64_t)j * a.KS;
-  const uint32_t hi = smem_u32(stage), lo = hi + kWsOpBytes;
+  const uint32_t hi = smem_u32(stage), lo = hi + WsNb<NB>::kOpBytes;
   const int koff = (k >> 3) * kWsLBO + (k & 7) * 16;
   const int ncopy = (G.K + 7) >> 3;
   for (int c = 0; c <= G.cb; ++c) {
-    const int off = c * kWsSBO + koff;
+    const int off = c * WsNb<NB>::kSBO + koff;
     if (live && c < ncopy) {
       cp_async16(hi + off, hrow + 8 * c);
       cp_async16(lo + off, lrow + 8 * c);
     } else {
       *reinterpret_cast<uint4*>(stage + off) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(stage + kWsOpBytes + off) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(stage + WsNb<NB>::kOpBytes + off) = make_uint4(0, 0, 0, 0);
     }
   }
 }
 
 // Feature K of neighbour k = the rating r, as bf16 hi and lo, written by the
 // lane that copied chunk cb of that neighbour, after its copy completed.
-__device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r,
-                                                int lane) {
-  const int k = lane;
-  const int off = G.cb * kWsSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
+template <int NB>
+__device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r, int k) {
+  const int off = G.cb * WsNb<NB>::kSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
   const __nv_bfloat16 h = __float2bfloat16_rn(r);
   *reinterpret_cast<__nv_bfloat16*>(stage + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(stage + kWsOpBytes + off) =
+  *reinterpret_cast<__nv_bfloat16*>(stage + WsNb<NB>::kOpBytes + off) =
       __float2bfloat16_rn(r - __bfloat162float(h));
 }
 
@@ -266,18 +272,24 @@ __host__ __device__ __forceinline__ int ws_slot(uint32_t n, int S) {
 
 // Copies of a warp's previous stage are waited for, patched, made visible to
 // the tensor cores and signalled once its next stage has been issued.
+template <int NB>
 __device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
                                           int lane) {
   const int ss = ws_slot(m, S);
-  ws_patch_rating(G, w.stages + ss * kWsStageBytes, w.rating[ss * kWsNb + lane], lane);
+#pragma unroll
+  for (int t = 0; t < NB / 32; ++t)
+    ws_patch_rating<NB>(G, w.stages + ss * WsNb<NB>::kStageBytes, w.rating[ss * NB + lane + 32 * t],
+                        lane + 32 * t);
   fence_proxy_async_smem();
   mbar_arrive(&w.full[ss]);
 }
 
+template <int NB>
 __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
                                           int S, int* counter) {
+  constexpr int NL = NB / 32;  // neighbours per lane
   const int t = threadIdx.x;
-  const int wg = t >> 5, lane = t & 31, k = lane;
+  const int wg = t >> 5, lane = t & 31;
   const int nrows = (int)(a.row_end - a.row_begin);
   // a warp owns S / 4 ring slots and keeps that many of its stages in flight
   // (up to four): the copies of the oldest are waited for only when a newer
@@ -312,27 +324,39 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
     if (t == 0)
       wk = next_slot < nrows && row >= 0 ? __ldg(a.work + a.row_begin + next_slot)
                                          : make_int4(-1, 0, 0, 0);
-    const int nst_r = (e1 - e0 + kWsNb - 1) / kWsNb;
+    const int nst_r = (e1 - e0 + NB - 1) / NB;
     const int nst = nst_r > 0 ? nst_r : 1;
     const int st_first = (int)((uint32_t)(wg - (int)(n & 3u)) & 3u);
-    // neighbour id and rating of this lane for the warp's next stage (four
+    // neighbour ids and ratings of this lane for the warp's next stage (four
     // stages on), loaded while the current one is issued
-    int32_t jn = 0;
-    float rn = 0.f;
-    if (row >= 0 && st_first < nst && e0 + st_first * kWsNb + k < e1) {
-      jn = __ldg(a.idx + e0 + st_first * kWsNb + k);
-      rn = __ldg(a.val + e0 + st_first * kWsNb + k);
+    int32_t jn[NL];
+    float rn[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int k = lane + 32 * u;
+      jn[u] = 0;
+      rn[u] = 0.f;
+      if (row >= 0 && st_first < nst && e0 + st_first * NB + k < e1) {
+        jn[u] = __ldg(a.idx + e0 + st_first * NB + k);
+        rn[u] = __ldg(a.val + e0 + st_first * NB + k);
+      }
     }
     for (int st = st_first; st < nst; st += 4) {
       const uint32_t nn = n + (uint32_t)st;
       const int s = ws_slot(nn, S);
-      const int e = e0 + st * kWsNb;
-      const int cnt = row < 0 ? 0 : (e1 - e < kWsNb ? (e1 - e > 0 ? e1 - e : 0) : kWsNb);
-      const int32_t j = jn;
-      const float r = rn;
-      if (row >= 0 && e + 4 * kWsNb + k < e1) {
-        jn = __ldg(a.idx + e + 4 * kWsNb + k);
-        rn = __ldg(a.val + e + 4 * kWsNb + k);
+      const int e = e0 + st * NB;
+      const int cnt = row < 0 ? 0 : (e1 - e < NB ? (e1 - e > 0 ? e1 - e : 0) : NB);
+      int32_t j[NL];
+      float r[NL];
+#pragma unroll
+      for (int u = 0; u < NL; ++u) {
+        const int k = lane + 32 * u;
+        j[u] = jn[u];
+        r[u] = rn[u];
+        if (row >= 0 && e + 4 * NB + k < e1) {
+          jn[u] = __ldg(a.idx + e + 4 * NB + k);
+          rn[u] = __ldg(a.val + e + 4 * NB + k);
+        }
       }
       if (!ws_wait_warp(&w.empty[s], ((nn / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
         stop = true;
@@ -347,8 +371,12 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
         w.meta[s].cnt = cnt;
         w.meta[s].flags = (st == 0 ? 1 : 0) | (st == nst - 1 ? 2 : 0);
       }
-      if (cnt > 0) ws_gather_stage(G, a, w.stages + s * kWsStageBytes, cnt, j, lane);
-      w.rating[s * kWsNb + k] = k < cnt ? r : 0.f;
+#pragma unroll
+      for (int u = 0; u < NL; ++u) {
+        const int k = lane + 32 * u;
+        if (cnt > 0) ws_gather_stage<NB>(G, a, w.stages + s * WsNb<NB>::kStageBytes, cnt, j[u], k);
+        w.rating[s * NB + k] = k < cnt ? r[u] : 0.f;
+      }
       cp_async_commit();
       if (npend == lag) {
         // the oldest of lag + 1 outstanding copy groups has landed once at
@@ -358,9 +386,9 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
         else if (lag == 2) cp_async_wait<2>();
         else cp_async_wait<3>();
         if (lag == 0) {
-          ws_signal(G, w, S, nn, lane);
+          ws_signal<NB>(G, w, S, nn, lane);
         } else {
-          ws_signal(G, w, S, pend[0], lane);
+          ws_signal<NB>(G, w, S, pend[0], lane);
           pend[0] = lag > 1 ? pend[1] : nn;
           pend[1] = lag > 2 ? pend[2] : nn;
           pend[2] = nn;
@@ -379,10 +407,11 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   cp_async_wait<0>();
 #pragma unroll
   for (int i = 0; i < 3; ++i)
-    if (i < npend) ws_signal(G, w, S, pend[i], lane);
+    if (i < npend) ws_signal<NB>(G, w, S, pend[i], lane);
 }
 
 // ---------------------------------------------------------------- MMA --
+template <int NB>
 __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S, uint32_t tmem) {
   const uint32_t idesc = idesc_bf16_mn(128, G.NP);
   const uint32_t base = smem_u32(w.stages);
@@ -401,11 +430,11 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
     }
     const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
     if (m.cnt > 0) {
-      const uint32_t hi = base + (uint32_t)s * kWsStageBytes, lo = hi + kWsOpBytes;
+      const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
       // K-steps of 16 neighbours: two 8-neighbour groups (2 LBO) apart
       for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
-        const uint64_t dh = smem_desc_kmajor(hi + kk * 2 * kWsLBO, kWsLBO, kWsSBO);
-        const uint64_t dl = smem_desc_kmajor(lo + kk * 2 * kWsLBO, kWsLBO, kWsSBO);
+        const uint64_t dh = smem_desc_kmajor(hi + kk * 2 * kWsLBO, kWsLBO, WsNb<NB>::kSBO);
+        const uint64_t dl = smem_desc_kmajor(lo + kk * 2 * kWsLBO, kWsLBO, WsNb<NB>::kSBO);
         tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
         tc_mma_bf16(acc, dh, dl, idesc, 1u);
         tc_mma_bf16(acc, dl, dh, idesc, 1u);
@@ -741,11 +770,12 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
   }
 }
 
+template <int NB>
 __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C, int* counter,
                                                  int* status) {
   extern __shared__ __align__(1024) uint8_t smem_ws[];
   const WsGeom G(a.K);
-  const WsShared w = ws_carve(smem_ws, G, S, C);
+  const WsShared w = ws_carve(smem_ws, G, S, C, NB);
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -767,7 +797,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
     mbar_fence_init();
   }
   // operand chunks past the last written one (features beyond K) stay zero
-  for (int e = threadIdx.x; e < S * kWsStageBytes / 16; e += blockDim.x)
+  for (int e = threadIdx.x; e < S * WsNb<NB>::kStageBytes / 16; e += blockDim.x)
     reinterpret_cast<uint4*>(w.stages)[e] = make_uint4(0, 0, 0, 0);
   {  // this g's trailing-update schedule, rounds counted from its first
     const unsigned short* rr = kWsUnitRound[G.g - kWsUnitGMin];
@@ -785,11 +815,11 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
   tc_fence_after();
   const uint32_t tmem = *w.taddr;
   if (warp < 4) {
-    ws_gather(a, G, w, S, counter);
+    ws_gather<NB>(a, G, w, S, counter);
   } else if (warp < 8) {
     ws_drain(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
-    if ((threadIdx.x & 31) == 0) ws_mma(G, w, S, tmem);
+    if ((threadIdx.x & 31) == 0) ws_mma<NB>(G, w, S, tmem);
   } else if (warp - kWsConsWarp0 < C) {
     ws_consume(a, G, w, C);
   }
@@ -819,17 +849,26 @@ __global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, in
 
 }  // namespace
 
+// Sides whose rows average 256 or more ratings (the movies of a
+// Netflix-shaped set) take 64 neighbours per stage: half the stage hand-offs
+// per neighbour; the others 32, which wastes less of the last stage of a
+// short row.
+int ws_stage_neighbours(int64_t nnz, int64_t R) {
+  return R > 0 && nnz >= kWsLongRow * R ? 64 : 32;
+}
+
 bool ws_supported(int K) {
   const int g = (K + 8) / 8;  // tiles per side of the bordered matrix
   return K >= 8 && K + 1 <= 128 && g >= kWsUnitGMin && g <= kWsUnitGMax;
 }
 
 // Stages (a multiple of 4, one or more ring slots per gather warp) and
-// consumer warps for latent dimension K.  With `cons` > 0 that many
-// consumers (if they fit) and the deepest ring up to 16 stages that fits;
+// consumer warps for latent dimension K and nb neighbours per stage.  With
+// `cons` > 0 that many consumers (as many as fit, if fewer) and the deepest
+// ring up to 16 stages that fits;
 // otherwise 8 stages if at least 3 consumers fit beside them, else 4 stages
 // and as many consumers as fit.
-int ws_config(int K, int cons, int* S, int* C) {
+int ws_config(int K, int cons, int nb, int* S, int* C) {
   const WsGeom G(K);
   int dev = 0, max_smem = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -839,14 +878,15 @@ int ws_config(int K, int cons, int* S, int* C) {
   }
   auto fit_cons = [&](int s) {
     int c = kWsMaxCons;
-    while (c > 0 && ws_smem_bytes(G, s, c) > max_smem) --c;
+    while (c > 0 && ws_smem_bytes(G, s, c, nb) > max_smem) --c;
     return c;
   };
   int s = 8, c = 0;
   if (cons > 0) {
     c = std::min(cons, kWsMaxCons);
     s = 16;
-    while (s > 4 && ws_smem_bytes(G, s, c) > max_smem) s -= 4;
+    while (s > 4 && ws_smem_bytes(G, s, c, nb) > max_smem) s -= 4;
+    while (c > 1 && ws_smem_bytes(G, s, c, nb) > max_smem) --c;  // more than fit: cut
   } else {
     c = fit_cons(s);
     if (c < 3) {
@@ -854,27 +894,29 @@ int ws_config(int K, int cons, int* S, int* C) {
       c = fit_cons(s);
     }
   }
-  if (c < 1 || ws_smem_bytes(G, s, c) > max_smem) return BPMF_EINVAL;
+  if (c < 1 || ws_smem_bytes(G, s, c, nb) > max_smem) return BPMF_EINVAL;
   *S = s;
   *C = c;
   return BPMF_OK;
 }
 
-int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int* counter, int* status,
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* counter, int* status,
                    cudaStream_t st, int64_t* launches) {
   const int64_t nrows = a.row_end - a.row_begin;
   if (nrows <= 0) return BPMF_OK;
+  if (nb != 32 && nb != 64) return BPMF_EINVAL;
   int S = 0, C = 0;
-  BPMF_TRY(ws_config(a.K, cons, &S, &C));
+  BPMF_TRY(ws_config(a.K, cons, nb, &S, &C));
   const WsGeom G(a.K);
-  const int smem = ws_smem_bytes(G, S, C);
-  BPMF_CUDA_CHECK(cudaFuncSetAttribute(row_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int smem = ws_smem_bytes(G, S, C, nb);
+  auto kern = nb == 64 ? row_ws<64> : row_ws<32>;
+  BPMF_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPMF_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
   ws_base_kernel<<<1, 128, 0, st>>>(a, a.wsbase);
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   const int grid = (int)std::min<int64_t>(num_sms, nrows);
-  row_ws<<<grid, 32 * (kWsConsWarp0 + C), smem, st>>>(a, S, C, counter, status);
+  kern<<<grid, 32 * (kWsConsWarp0 + C), smem, st>>>(a, S, C, counter, status);
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   return BPMF_OK;

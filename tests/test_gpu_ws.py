@@ -18,6 +18,8 @@ CASES = {
     "k8": (lambda: synth.powerlaw(3000, 800, 40000, 8, 0.5, 0.9, seed=54), 8),
     "k33": (lambda: synth.powerlaw(4000, 900, 60000, 33, 0.5, 0.9, seed=55), 33),
     "k96": (lambda: synth.uniform(2500, 400, 50000, 96, seed=56), 96),
+    # movies averaging ~1000 ratings: that side's stages hold 64 neighbours
+    "long_k100": (lambda: synth.powerlaw(24000, 300, 330000, 100, 0.5, 0.9, seed=57), 100),
 }
 _cache = {}
 
@@ -83,7 +85,8 @@ def test_persistent_rows_chain_is_deterministic(gpu_lib):
 
 
 @pytest.mark.parametrize("name,cons", [("wide_k100", 1), ("wide_k100", 2), ("wide_k100", 6),
-                                       ("k8", 1), ("k33", 2), ("k127", 1)])
+                                       ("k8", 1), ("k33", 2), ("k127", 1), ("long_k100", 1),
+                                       ("long_k100", 3), ("long_k100", 7)])
 def test_consumer_counts_and_ring_depths(gpu_lib, name, cons):
     """Fewer consumer warps leave room for a deeper stage ring (a gather warp
     then keeps up to four of its stages in flight); every such
