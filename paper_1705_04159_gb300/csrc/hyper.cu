@@ -145,7 +145,7 @@ __global__ void scatter_final(const double* __restrict__ part, int blocks, int K
 // FP64 square roots and divisions are many FP64 instructions each, so the
 // pivot's root and reciprocal are taken once, by thread 0, and the column is
 // scaled by the reciprocal.
-__device__ bool cta_cholesky(double* A, int K, int* bad) {
+__device__ bool cta_cholesky(double* A, int K, int* bad, double* rdiag = nullptr) {
   __shared__ double s_rd;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) *bad = 0;
@@ -157,15 +157,16 @@ __device__ bool cta_cholesky(double* A, int K, int* bad) {
       if (!(piv > 0.0)) *bad = 1;
       A[k * K + k] = d;
       s_rd = 1.0 / d;
+      if (rdiag != nullptr) rdiag[k] = s_rd;
     }
     __syncthreads();
     const double rd = s_rd;
     for (int i = k + 1 + tid; i < K; i += nt) A[i * K + k] *= rd;
     __syncthreads();
-    const int m = K - k - 1;
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i * K + j] -= A[i * K + k] * A[j * K + k];
+    // trailing update of the lower triangle, a warp per row
+    for (int i = k + 1 + (tid >> 5); i < K; i += nt >> 5) {
+      const double aik = A[i * K + k];
+      for (int j = k + 1 + (tid & 31); j <= i; j += 32) A[i * K + j] = fma(-aik, A[j * K + k], A[i * K + j]);
     }
     __syncthreads();
   }
@@ -212,6 +213,32 @@ __device__ void cta_tri_inverse(const double* L, double* Linv, int K) {
     }
   }
   __syncthreads();
+}
+
+// T = L^-1 for lower-triangular L (row-major, K x K, in global memory; rdiag
+// = 1 / L_ii), one warp per column (blockIdx.x = j): L t_j = e_j by forward
+// substitution,
+// each row's dot product split across the lanes and summed by shuffles.  The
+// columns are independent, so K CTAs run them side by side.
+__global__ void __launch_bounds__(32) tri_inverse_cols(const double* __restrict__ L,
+                                                       const double* __restrict__ rdiag, double* T,
+                                                       int K, const double* ok) {
+  __shared__ double col[kMaxK];
+  if (ok != nullptr && *ok == 0.0) return;
+  const int j = blockIdx.x, lane = threadIdx.x;
+  for (int i = lane; i < j; i += 32) T[i * K + j] = 0.0;
+  for (int i = j; i < K; ++i) {
+    double part = 0.0;
+    for (int k = j + lane; k < i; k += 32) part = fma(L[i * K + k], col[k], part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double v = ((i == j ? 1.0 : 0.0) - part) * rdiag[i];
+    if (lane == 0) {
+      col[i] = v;
+      T[i * K + j] = v;
+    }
+    __syncwarp();
+  }
 }
 
 // C = A^T A (symmetric)
@@ -315,19 +342,20 @@ struct HyperArgs {
 //    (lower triangular with a positive diagonal, hence the Cholesky factor);
 //  * chol(beta* Lambda) = sqrt(beta*) B for B = C A (lower triangular with a
 //    positive diagonal and Lambda = B B^T), so mu = mu* + B^-T z / sqrt(beta*).
-// The steps with a chain through K (Cholesky, inverse, Bartlett draws, the
-// back substitution for mu) run in one CTA; B = C A and Lambda = B B^T, each
-// K^3 / 6 multiply-adds with no chain between rows, run one CTA per row.
-// Scratch (doubles): Mx | T | A | B (K*K each) | mu* | x (K each) | ...;
-// scr[5 K*K] = 1 once the factorisation succeeded (0: the later steps skip).
+// The Cholesky, the Bartlett draws and the back substitution for mu run in
+// one CTA; L_M^-1 runs one warp per column, and B = C A and Lambda = B B^T,
+// each K^3 / 6 multiply-adds with no chain between rows, one CTA per row.
+// Scratch (doubles): Mx | T | A | B (K*K each) | mu* (K) | ...; scr[5 K*K] = 1
+// once the factorisation succeeded (0: the later steps skip), followed by
+// 1 / diag(L_M) (K).
 
-// (3a) posterior, L_M, T = L_M^-1, Bartlett A and mu*, by one CTA
+// (3a) posterior, L_M, Bartlett A and mu*, by one CTA (T = L_M^-1 follows in
+// tri_inverse_cols)
 __global__ void __launch_bounds__(512) wishart_factor(HyperArgs a) {
   __shared__ int bad;
   const int K = a.K, KK = K * K;
   double* Mx = a.scr;          // J W*^-1 J, then its Cholesky factor L_M
-  double* T = Mx + KK;         // L_M^-1
-  double* A = T + KK;          // Bartlett A
+  double* A = Mx + 2 * KK;     // Bartlett A (L_M^-1 goes between the two)
   double* mus = A + 2 * KK;    // mu*
   double* ok = a.scr + 5 * KK;
   const double n = (double)a.n;
@@ -340,14 +368,13 @@ __global__ void __launch_bounds__(512) wishart_factor(HyperArgs a) {
     mus[k] = (a.beta0 * a.mu0[k] + n * a.xbar[k]) / (a.beta0 + n);
   __syncthreads();
   const double nu_s = a.nu0 + n;
-  if (!cta_cholesky(Mx, K, &bad)) {
+  if (!cta_cholesky(Mx, K, &bad, ok + 1)) {
     if (threadIdx.x == 0) {
       *ok = 0.0;
       atomicOr(a.status, kStatusNotPD);
     }
     return;
   }
-  cta_tri_inverse(Mx, T, K);
   cta_bartlett_A(A, K, nu_s, seed_key(a.seed), *a.tp, a.side, a.status);
   if (threadIdx.x == 0) *ok = 1.0;
 }
@@ -479,7 +506,7 @@ int launch_hyper(Handle* h, int s) {
     else launch_scatter<8>(sd.X, R, K, xbarf, part, blocks, st);
     scatter_final<<<(K * K + 255) / 256, 256, 0, st>>>(part, blocks, K, sd.S);
     BPMF_CUDA_CHECK(cudaGetLastError());
-    h->kernels += 4;
+    h->kernels += 5;
   }
   HyperArgs a;
   a.xbar = sd.xbar;
@@ -502,6 +529,8 @@ int launch_hyper(Handle* h, int s) {
   {
     PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
     wishart_factor<<<1, 512, 0, st>>>(a);
+    tri_inverse_cols<<<K, 32, 0, st>>>(a.scr, a.scr + 5 * K * K + 1, a.scr + K * K, K,
+                                       a.scr + 5 * K * K);
     wishart_b<<<K, 128, 0, st>>>(a);
     wishart_lam<<<K, 128, 0, st>>>(a);
     wishart_mu<<<1, 128, 0, st>>>(a);
