@@ -449,10 +449,10 @@ def main():
     else:
         achieved, peak, unit = f_chol / (t_ms / 1e3) / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
     # DRAM bytes per launch from one ncu capture of the persistent row kernel
-    # on the 120k-user, 18M-rating case (users launch: 166.8 MB read + 27.9 MB
+    # on the 120k-user, 18M-rating case (users launch: 166.3 MB read + 28.1 MB
     # written), scaled to the full launch by ratings (x5: the per-rating index
     # and value reads dominate)
-    traffic = (166.8e6 + 27.9e6) * 5 if (args.workload == "netflix" and side == 0 and
+    traffic = (166.3e6 + 28.1e6) * 5 if (args.workload == "netflix" and side == 0 and
                                           mixed["thresholds"][0][3] == 1) else None
     roofline = {"kernel": f"row update, {'users' if side == 0 else 'movies'} side",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
