@@ -38,16 +38,21 @@ __global__ void colsum_partial(const float* __restrict__ X, int64_t R, int K,
   const int64_t r1 = min(R, r0 + per);
   double acc = 0.0;
   if (k < K) {
-    float chunk = 0.f;
-    int cnt = 0;
-    for (int64_t r = r0 + grp; r < r1; r += 2) {
-      chunk += X[r * K + k];
-      if (++cnt == 64) {
-        acc += (double)chunk;
-        chunk = 0.f;
-        cnt = 0;
-      }
+    // 64 rows of this group at a time, as eight loads in flight, summed in
+    // FP32 and flushed to FP64
+    int64_t r = r0 + grp;
+    for (; r + 2 * 63 < r1; r += 2 * 64) {
+      float c8[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c8[q] = 0.f;
+#pragma unroll
+      for (int t8 = 0; t8 < 64; t8 += 8)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c8[q] += X[(r + 2 * (t8 + q)) * K + k];
+      acc += (double)(((c8[0] + c8[1]) + (c8[2] + c8[3])) + ((c8[4] + c8[5]) + (c8[6] + c8[7])));
     }
+    float chunk = 0.f;
+    for (; r < r1; r += 2) chunk += X[r * K + k];
     acc += (double)chunk;
   }
   if (grp == 1) half[k] = acc;
@@ -59,8 +64,14 @@ __global__ void colsum_final(const double* __restrict__ part, int blocks, int K,
                              double* __restrict__ xbar, float* __restrict__ xbarf) {
   const int k = threadIdx.x;
   if (k < K) {
-    double s = 0.0;
-    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * K + k];
+    // four chains over the blocks (b = q mod 4), combined in a fixed order
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int b = 0;
+    for (; b + 4 <= blocks; b += 4)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += part[(int64_t)(b + q) * K + k];
+    for (; b < blocks; ++b) s4[0] += part[(int64_t)b * K + k];
+    double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     s /= (double)R;
     xbar[k] = s;
     xbarf[k] = (float)s;
@@ -71,12 +82,13 @@ __global__ void colsum_final(const double* __restrict__ part, int blocks, int K,
 // tile at rows ty*TM.., cols tx*TM..; only tiles with ty >= tx (the lower
 // triangle) are accumulated; the upper triangle is mirrored at the end.
 template <int TM>
-__global__ void __launch_bounds__(256) scatter_partial(const float* __restrict__ X, int64_t R,
+__global__ void __launch_bounds__(256, 2) scatter_partial(const float* __restrict__ X, int64_t R,
                                                        int K, const float* __restrict__ xbarf,
                                                        double* __restrict__ part) {
   constexpr int KP = 16 * TM;
-  constexpr int CH = 32;
-  __shared__ float xs[CH][KP + 1];
+  constexpr int CH = 16;
+  constexpr int PER = (CH * KP + 255) / 256;  // chunk elements per thread
+  __shared__ float xs[2][CH][KP + 1];
   const int tid = threadIdx.x;
   const int ty = tid >> 4, tx = tid & 15;
   const bool active = ty >= tx;
@@ -88,23 +100,41 @@ __global__ void __launch_bounds__(256) scatter_partial(const float* __restrict__
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TM; ++b) acc[a][b] = 0.f;
+  // centred values of a chunk, this thread's share, into registers
+  float v[PER];
+  auto fetch = [&](int64_t c0) {
+    const int cnt = (int)min((int64_t)CH, r1 - c0);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      const int rr = e / KP, k = e % KP;
+      v[q] = (e < CH * KP && rr < cnt && k < K) ? X[(c0 + rr) * K + k] - xbarf[k] : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + 256 * q;
+      if (e < CH * KP) xs[buf][e / KP][e % KP] = v[q];
+    }
+  };
+  int buf = 0;
+  if (r0 < r1) {
+    fetch(r0);
+    stash(0);
+  }
+  __syncthreads();
   for (int64_t c0 = r0; c0 < r1; c0 += CH) {
     const int cnt = (int)min((int64_t)CH, r1 - c0);
-    __syncthreads();
-    for (int e = tid; e < CH * KP; e += 256) {
-      const int rr = e / KP, k = e % KP;
-      float v = 0.f;
-      if (rr < cnt && k < K) v = X[(c0 + rr) * K + k] - xbarf[k];
-      xs[rr][k] = v;
-    }
-    __syncthreads();
+    const bool more = c0 + CH < r1;
+    if (more) fetch(c0 + CH);  // in flight while this chunk is used
     if (active) {
       for (int rr = 0; rr < cnt; ++rr) {
         float a[TM], b[TM];
 #pragma unroll
         for (int q = 0; q < TM; ++q) {
-          a[q] = xs[rr][ty * TM + q];
-          b[q] = xs[rr][tx * TM + q];
+          a[q] = xs[buf][rr][ty * TM + q];
+          b[q] = xs[buf][rr][tx * TM + q];
         }
 #pragma unroll
         for (int p = 0; p < TM; ++p)
@@ -112,6 +142,9 @@ __global__ void __launch_bounds__(256) scatter_partial(const float* __restrict__
           for (int q = 0; q < TM; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
       }
     }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
   }
   if (active) {
     double* out = part + (int64_t)blockIdx.x * K * K;
@@ -131,8 +164,13 @@ __global__ void scatter_final(const double* __restrict__ part, int blocks, int K
   if (e >= K * K) return;
   const int i = e / K, j = e % K;
   if (j > i) return;
-  double s = 0.0;
-  for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * K * K + i * K + j];
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};  // four chains, combined in a fixed order
+  int b = 0;
+  for (; b + 4 <= blocks; b += 4)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s4[q] += part[(int64_t)(b + q) * K * K + i * K + j];
+  for (; b < blocks; ++b) s4[0] += part[(int64_t)b * K * K + i * K + j];
+  const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   S[i * K + j] = s;
   S[j * K + i] = s;
 }
@@ -172,7 +210,7 @@ __device__ bool cta_cholesky(double* A, int K, int* bad, double* rdiag = nullptr
   }
   for (int e = tid; e < K * K; e += nt) {
     const int i = e / K, j = e % K;
-    if (j > i) A[e] = 0.0;
+    if (j > i) A[i * K + j] = 0.0;
   }
   __syncthreads();
   const bool ok = *bad == 0;

@@ -98,13 +98,21 @@ __global__ void test_errors(const float* __restrict__ U, const float* __restrict
 __global__ void test_final(const double* __restrict__ part, int blocks, int64_t n,
                            double* __restrict__ out, const uint32_t* __restrict__ tp,
                            int64_t burnin, int64_t* __restrict__ navg) {
-  if (threadIdx.x == 0) {
+  // lane l sums blocks l, l + 32, ..; the 32 partial sums are combined by a
+  // fixed shuffle tree, so the order never depends on timing
+  const int lane = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = lane; i < blocks; i += 32) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
     if ((int64_t)*tp >= burnin) *navg += 1;
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < blocks; ++i) {
-      a += part[2 * i];
-      b += part[2 * i + 1];
-    }
     out[0] = n > 0 ? sqrt(a / (double)n) : 0.0;
     out[1] = n > 0 ? sqrt(b / (double)n) : 0.0;
   }
