@@ -10,27 +10,29 @@
 // One CTA per SM takes rows of the degree order from a global counter
 // (largest first) and runs them through a pipeline of warp roles:
 //   gather (warps 0-3): copies the bf16 hi/lo shadow rows of the neighbours,
-//     32 per stage, with 16-byte cp.async straight into MN-major operand
-//     tiles (feature-contiguous 8 x 16-byte core matrices: chunk c of
-//     neighbour k at c * 512 + (k / 8) * 128 + (k % 8) * 16) into a ring of
-//     stages, and patches the rating in as feature K;
-//   MMA (warp 8, one thread): per stage hi.hi + hi.lo + lo.hi into one of two
-//     FP32 accumulators in tensor memory (G = X^T X with X the stage's
-//     neighbours x features; lo.lo, ~2^-16 relative, is dropped);
+//     NB per stage (32, or 64 on a side whose rows average 256 or more
+//     ratings), with 16-byte cp.async straight into MN-major operand tiles
+//     (feature-contiguous 8 x 16-byte core matrices: chunk c of neighbour k
+//     at c * 16 NB + (k / 8) * 128 + (k % 8) * 16) into a ring of stages, and
+//     patches the rating in as feature K;
+//   MMA (warp 8, one thread): per 16 neighbours hi.hi + hi.lo + lo.hi into
+//     one of two FP32 accumulators in tensor memory (G = X^T X with X the
+//     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped);
 //   drain (warps 4-7, thread m = tensor-memory lane m = matrix row m):
 //     forms A = base + alpha G (base = bordered [[Lambda_s, b0], [b0^T, 0]])
 //     and writes its lower triangle as 8 x 8 FP32 tiles into a free
 //     consumer slot, releasing the accumulator for the next row;
 //   consumers (warps 9.., one row each): blocked right-looking Cholesky of
-//     the slot (per 8-column panel: the diagonal tile by shuffles, the panel
-//     by forward substitution, the trailing tiles as register-blocked
-//     8 x 8 x 8 updates), then u = L^-T (y + z) by back substitution.
+//     the slot (per 8-column panel: the diagonal tile in registers by every
+//     lane, the panel by forward substitution, the trailing tiles as
+//     register-blocked half-tile updates on a bank-aware lane schedule),
+//     then u = L^-T (y + z) by back substitution.
 // So the tensor cores, the gathers and the FP32 factorisations of up to
 // seven rows per SM overlap, with no CTA-wide barrier on the way.
 //
-// Every mbarrier wait is bounded; on a timeout the CTA records
-// kStatusTimeout, every role leaves its loop, outstanding copies and MMAs
-// are waited for (bounded) and the tensor memory is freed.
+// Every mbarrier wait polls with a wall-clock bound; on a timeout the CTA
+// records kStatusTimeout, every role leaves its loop, outstanding copies and
+// MMAs are waited for (bounded) and the tensor memory is freed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
