@@ -477,7 +477,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded Netflix-shaped ratings generated on the device)",
+            "data": f"synthetic (seeded {ds.name}-shaped ratings generated on the device)",
             "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train + "
                                    f"{len(ds.test_row)} test ratings, K={K}",
                        "path": args.path, "global_batch": rows, "parallelism": f"replicas{world}",
@@ -520,7 +520,7 @@ def reference_arm(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded Netflix-shaped ratings)",
+            "data": f"synthetic (seeded {ds.name}-shaped ratings)",
             "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train ratings, K={K}",
                        "global_batch": ds.M + ds.N, "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
