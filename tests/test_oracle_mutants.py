@@ -2,9 +2,11 @@
 
 Each case plants one mistake in a copy of the oracle's C source (a dropped
 term, an off-by-one degree of freedom, a transposed operand, a flipped sign,
-a missing factor, a wrong index), builds it with gcc on the CPU and runs the
-oracle's pin tests against that build in a fresh interpreter: at least one
-pin must fail.  Nothing here touches a GPU or the CUDA library.
+a missing factor, a wrong weight, a wrong generator constant, swapped
+normals, a truncated acceptance test, uncentred ratings, reversed ties),
+builds it with gcc on the CPU and runs the oracle's pin tests against that
+build in a fresh interpreter: at least one pin must fail.  Nothing here
+touches a GPU or the CUDA library.
 """
 import os
 import subprocess
@@ -28,6 +30,16 @@ MUTANTS = {
     "drop_alpha": ("P[a * K + c] += alpha * v[a] * v[c];", "P[a * K + c] += v[a] * v[c];"),
     # posterior mean weighting the sample mean by 1 instead of n
     "mu_star_weight": ("(beta0 * mu0[a] + dn * xbar[a])", "(beta0 * mu0[a] + xbar[a])"),
+    # a Philox round constant off by one
+    "philox_constant": ("(uint64_t)0xD2511F53u * (uint64_t)x0", "(uint64_t)0xD2511F55u * (uint64_t)x0"),
+    # Box-Muller with the sine and cosine normals swapped
+    "box_muller_swap": ("*z0 = r * cos(2.0 * pi * u2);", "*z0 = r * sin(2.0 * pi * u2);"),
+    # Gamma acceptance without the log(v) term
+    "gamma_accept": ("+ d - d * v + d * log(v))", "+ d - d * v)"),
+    # ratings not centred by the training mean
+    "no_centring": ("cval[p] = (double)val[e] - mean;", "cval[p] = (double)val[e];"),
+    # degree ties broken by descending row id
+    "degree_ties": ("return a < b ? -1 : (a > b ? 1 : 0);", "return a > b ? -1 : (a < b ? 1 : 0);"),
 }
 
 RUNNER = r"""
@@ -38,8 +50,10 @@ oracle._SRC = {src!r}
 oracle._LIB = {lib!r}
 import pytest
 sys.exit(pytest.main(["-q", "-x", "--no-header", "-p", "no:cacheprovider",
+                      os.path.join({root!r}, "tests", "test_oracle_rng.py"),
                       os.path.join({root!r}, "tests", "test_oracle_hyper.py"),
-                      os.path.join({root!r}, "tests", "test_oracle_row.py")]))
+                      os.path.join({root!r}, "tests", "test_oracle_row.py"),
+                      os.path.join({root!r}, "tests", "test_oracle_structure.py")]))
 """
 
 
