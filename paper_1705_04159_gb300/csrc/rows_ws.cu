@@ -214,10 +214,6 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 
-__device__ __forceinline__ uint32_t bf16_bits(float x) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-
 // kind::f16 instruction descriptor, BF16 operands both MN-major (bits 15, 16).
 __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
   return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
