@@ -110,6 +110,12 @@ namespace {
 
 int valid_side(int side) { return side == BPMF_USERS || side == BPMF_MOVIES; }
 
+// Records which entry point rejected its arguments and returns BPMF_EINVAL.
+int einval(const char* what) {
+  set_error("%s: invalid argument (null handle, side, pointer or size)", what);
+  return BPMF_EINVAL;
+}
+
 int sweep_one(Handle* h, int s) {
   BPMF_TRY(launch_sweep(h, s));
   return BPMF_OK;
@@ -477,14 +483,14 @@ int bpmf_set_test(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col,
 
 int bpmf_sample_hyper(bpmf_t* hh, int side) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side)) return BPMF_EINVAL;
+  if (!h || !valid_side(side)) return einval("bpmf_sample_hyper");
   BPMF_TRY(launch_hyper(h, side));
   return check_status(h, "bpmf_sample_hyper");
 }
 
 int bpmf_sweep(bpmf_t* hh, int side) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side)) return BPMF_EINVAL;
+  if (!h || !valid_side(side)) return einval("bpmf_sweep");
   if (!h->side[side].have_hyper) {
     set_error("bpmf_sweep: no hyperparameters drawn or set for this side");
     return BPMF_ESTATE;
@@ -496,7 +502,7 @@ int bpmf_sweep(bpmf_t* hh, int side) {
 
 int bpmf_step(bpmf_t* hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_step");
   BPMF_TRY(step_async(h));
   const int rc = check_status(h, "bpmf_step");
   if (rc == BPMF_OK && h->use_graph && h->timing) BPMF_TRY(resolve_graph_timers(h));
@@ -505,7 +511,7 @@ int bpmf_step(bpmf_t* hh) {
 
 int bpmf_set_graph(bpmf_t* hh, int enable) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_set_graph");
   drop_graph(h);
   h->use_graph = enable != 0;
   return BPMF_OK;
@@ -514,7 +520,7 @@ int bpmf_set_graph(bpmf_t* hh, int enable) {
 int bpmf_predict(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col, float* out,
                  uint32_t flags) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || n < 0 || (n > 0 && (!row || !col || !out))) return BPMF_EINVAL;
+  if (!h || n < 0 || (n > 0 && (!row || !col || !out))) return einval("bpmf_predict");
   if (n == 0) return BPMF_OK;
   const bool dev = (flags & BPMF_DEVPTR) != 0;
   int32_t *d_row = nullptr, *d_col = nullptr;
@@ -543,7 +549,7 @@ int bpmf_predict(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col, 
 
 int bpmf_test_rmse(bpmf_t* hh, double* rmse_sample, double* rmse_mean) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_test_rmse");
   if (!h->have_rmse) {
     set_error("bpmf_test_rmse: no test set or no iteration yet");
     return BPMF_ESTATE;
@@ -558,7 +564,7 @@ int bpmf_test_rmse(bpmf_t* hh, double* rmse_sample, double* rmse_mean) {
 
 int bpmf_get_state(bpmf_t* hh, float* U, float* V, double* hyper, int64_t* iter, uint32_t flags) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_get_state");
   const cudaMemcpyKind kind = (flags & BPMF_DEVPTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const int K = h->K;
   const int64_t KK = (int64_t)K * K;
@@ -581,7 +587,7 @@ int bpmf_get_state(bpmf_t* hh, float* U, float* V, double* hyper, int64_t* iter,
 int bpmf_set_state(bpmf_t* hh, const float* U, const float* V, const double* hyper, int64_t iter,
                    uint32_t flags) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || iter < 0) return BPMF_EINVAL;
+  if (!h || iter < 0) return einval("bpmf_set_state");
   const cudaMemcpyKind kind = (flags & BPMF_DEVPTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const int K = h->K;
   const int64_t KK = (int64_t)K * K;
@@ -624,7 +630,7 @@ int bpmf_set_state(bpmf_t* hh, const float* U, const float* V, const double* hyp
 int bpmf_get_structure(bpmf_t* hh, int side, int64_t* ptr, int32_t* idx, float* val, int32_t* perm,
                        double* mean) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side)) return BPMF_EINVAL;
+  if (!h || !valid_side(side)) return einval("bpmf_get_structure");
   SideDev& sd = h->side[side];
   cudaStream_t st = h->stream;
   if (ptr) BPMF_CUDA_CHECK(cudaMemcpyAsync(ptr, sd.ptr, sizeof(int64_t) * (sd.R + 1), cudaMemcpyDeviceToHost, st));
@@ -638,7 +644,7 @@ int bpmf_get_structure(bpmf_t* hh, int side, int64_t* ptr, int32_t* idx, float* 
 
 int bpmf_get_hyper_stats(bpmf_t* hh, int side, double* xbar, double* S) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side)) return BPMF_EINVAL;
+  if (!h || !valid_side(side)) return einval("bpmf_get_hyper_stats");
   SideDev& sd = h->side[side];
   if (!sd.have_stats) return BPMF_ESTATE;
   const int K = h->K;
@@ -650,7 +656,7 @@ int bpmf_get_hyper_stats(bpmf_t* hh, int side, double* xbar, double* S) {
 
 int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[5]) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side) || !thresholds) return BPMF_EINVAL;
+  if (!h || !valid_side(side) || !thresholds) return einval("bpmf_get_thresholds");
   const SideDev& sd = h->side[side];
   thresholds[0] = sd.tiny_max;
   thresholds[1] = sd.light_max;
@@ -664,13 +670,16 @@ int bpmf_get_thresholds(bpmf_t* hh, int side, int64_t thresholds[5]) {
 
 int bpmf_set_thresholds(bpmf_t* hh, int side, const int64_t thresholds[5]) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side) || !thresholds) return BPMF_EINVAL;
+  if (!h || !valid_side(side) || !thresholds) return einval("bpmf_set_thresholds");
   if (h->cfg.path == BPMF_PATH_PLAIN) {
     // one kernel for every row: only the values in effect are accepted
     int64_t cur[5];
     bpmf_get_thresholds(hh, side, cur);
     for (int i = 0; i < 5; ++i)
-      if (thresholds[i] != cur[i]) return BPMF_EINVAL;
+      if (thresholds[i] != cur[i]) {
+        set_error("bpmf_set_thresholds: the plain path keeps its single schedule");
+        return BPMF_EINVAL;
+      }
     return BPMF_OK;
   }
   return set_thresholds(h, side, thresholds);
@@ -678,7 +687,7 @@ int bpmf_set_thresholds(bpmf_t* hh, int side, const int64_t thresholds[5]) {
 
 int bpmf_get_sweep_info(bpmf_t* hh, int side, int64_t bins[4], int64_t* fp64_rows) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h || !valid_side(side)) return BPMF_EINVAL;
+  if (!h || !valid_side(side)) return einval("bpmf_get_sweep_info");
   SideDev& sd = h->side[side];
   if (bins)
     for (int b = 0; b < 4; ++b) bins[b] = sd.bin_count[b];
@@ -778,7 +787,7 @@ extern "C" {
 
 int bpmf_set_timing(bpmf_t* hh, int enable) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_set_timing");
   BPMF_TRY(resolve_timers(h));
   for (int i = 0; i < BPMF_NUM_TIMERS; ++i) {
     h->t_ms[i] = 0.0;
@@ -791,7 +800,7 @@ int bpmf_set_timing(bpmf_t* hh, int enable) {
 
 int bpmf_get_timing(bpmf_t* hh, double* ms, int64_t* phase_count, int64_t* kernels) {
   Handle* h = reinterpret_cast<Handle*>(hh);
-  if (!h) return BPMF_EINVAL;
+  if (!h) return einval("bpmf_get_timing");
   if (!h->timing) return BPMF_ESTATE;
   BPMF_TRY(resolve_timers(h));
   for (int i = 0; i < BPMF_NUM_TIMERS; ++i) {

@@ -122,3 +122,18 @@ def test_struct_mirrors_match_the_c_layout(tmp_path, pyname, ctype):
                                           text=True).stdout.split()]
     assert got[0] == C.sizeof(cls)
     assert got[1:] == [getattr(cls, n).offset for n in names]
+
+
+@pytest.mark.parametrize("name,args", [
+    ("bpmf_sample_hyper", (0,)), ("bpmf_sweep", (1,)), ("bpmf_step", ()),
+    ("bpmf_set_graph", (1,)), ("bpmf_test_rmse", (None, None)),
+    ("bpmf_get_state", (None, None, None, None, 0)), ("bpmf_get_thresholds", (0, None)),
+    ("bpmf_get_sweep_info", (0, None, None)), ("bpmf_set_timing", (1,)),
+])
+def test_null_handle_is_rejected_with_a_message(libpath, name, args):
+    """Every entry point that takes a handle checks it before anything else
+    and says which call rejected its arguments."""
+    import paper_1705_04159_gb300 as bp
+    L = bp.lib()
+    assert getattr(L, name)(None, *args) == bp.EINVAL
+    assert L.bpmf_last_error().decode().startswith(name + ": invalid argument")
