@@ -163,28 +163,40 @@ BPMF_API int bpmf_step(bpmf_t *h);
 BPMF_API int bpmf_set_graph(bpmf_t *h, int enable);
 
 /* Predictions r = u_row . v_col + mean for n pairs from the current sample
- * into out[n] (float32).  Errors: EINVAL, ECUDA. */
+ * into out[n] (float32): the prediction step of Algorithm 1 under the model
+ * R ~= U V^T of paper Sec. I, with the training mean added back.  row and col
+ * are n int32 indices (host arrays, or device arrays with BPMF_DEVPTR, which
+ * then applies to out too); they are read during the call only.
+ * Errors: EINVAL (null handle or array, negative n, an index out of range),
+ * ECUDA. */
 BPMF_API int bpmf_predict(bpmf_t *h, int64_t n, const int32_t *row, const int32_t *col, float *out,
                  uint32_t flags);
 
 /* Test RMSE of the latest sample and of the running mean of predictions
- * (either pointer may be NULL).  Errors: ESTATE (no test set or no step). */
+ * (either pointer may be NULL): the RMSE Algorithm 1 reports each iteration,
+ * the mean taken over the iterations from `burnin` on.
+ * Errors: EINVAL (null handle), ESTATE (no test set or no step), ECUDA. */
 BPMF_API int bpmf_test_rmse(bpmf_t *h, double *rmse_sample, double *rmse_mean);
 
-/* Copies the state out.  U: M*K floats, V: N*K floats, hyper: 2*(K*K + K)
+/* Copies the state out (checkpointing; the paper has no counterpart, and the
+ * Philox counters carry no hidden state, so these parts are the whole state
+ * of the chain).  U: M*K floats, V: N*K floats, hyper: 2*(K*K + K)
  * doubles laid out as [Lambda_U (K*K), mu_U (K), Lambda_V (K*K), mu_V (K)],
  * iter: the iteration counter.  Any pointer may be NULL.  BPMF_DEVPTR
  * applies to U and V only.  Errors: ECUDA. */
 BPMF_API int bpmf_get_state(bpmf_t *h, float *U, float *V, double *hyper, int64_t *iter,
                    uint32_t flags);
 
-/* Replaces the state (same layouts as bpmf_get_state; NULL keeps a part).
+/* Replaces the state (resume from a checkpoint; same layouts as
+ * bpmf_get_state, host arrays read during the call; NULL keeps a part).
  * Setting `hyper` marks both sides' hyperparameters as drawn.
  * Errors: EINVAL (Lambda not SPD), ECUDA. */
 BPMF_API int bpmf_set_state(bpmf_t *h, const float *U, const float *V, const double *hyper,
                    int64_t iter, uint32_t flags);
 
-/* Copies one side's compressed structure (for checking): ptr (R+1 int64),
+/* Copies one side's compressed structure (for checking): the per-row
+ * rating lists Algorithm 1 loops over for every user and every movie.
+ * Host outputs: ptr (R+1 int64),
  * idx (nnz int32), val (nnz float32, centred), perm (R int32, rows by degree,
  * largest first, ties by row id), and the mean.  NULL skips a part.
  * Errors: EINVAL, ECUDA. */
@@ -192,7 +204,9 @@ BPMF_API int bpmf_get_structure(bpmf_t *h, int side, int64_t *ptr, int32_t *idx,
                        int32_t *perm, double *mean);
 
 /* Last hyperparameter statistics of `side`: the row mean xbar (K) and the
- * centred scatter S = sum (x - xbar)(x - xbar)^T (K*K), as float64.
+ * centred scatter S = sum (x - xbar)(x - xbar)^T (K*K), as float64 host
+ * arrays -- the sufficient statistics of the Normal-Wishart hyperparameter
+ * draw (paper Sec. II, Algorithm 1), kept from the last bpmf_sample_hyper.
  * Errors: EINVAL, ESTATE, ECUDA. */
 BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
 
@@ -205,7 +219,8 @@ BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
  * Errors: EINVAL. */
 BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *fp64_rows);
 
-/* The schedule in effect for `side`: thresholds[0] = tiny_max (-1: no
+/* The schedule in effect for `side` (the degree bins of paper Sec. IV-B;
+ * host output array): thresholds[0] = tiny_max (-1: no
  * rank-one bin), [1] = light_max, [2] = hub_min -- the configured values, the
  * defaults (tiny_max 0 on the BINNED and MIXED paths, light_max = tiny_max,
  * hub_min 8192) or the autotuned ones; [3] = the kernel of the heavy bin (0
@@ -237,7 +252,8 @@ BPMF_API int bpmf_set_thresholds(bpmf_t *h, int side, const int64_t thresholds[5
 #define BPMF_T_PREDICT 5       /* test predictions and RMSE */
 #define BPMF_NUM_TIMERS 6
 
-/* Turns per-phase CUDA-event timing on (1) or off (0) and clears the
+/* Measurement only (the paper has no counterpart).
+ * Turns per-phase CUDA-event timing on (1) or off (0) and clears the
  * accumulated times.  When on, each timed phase is bracketed by two events
  * recorded on the handle's stream.  Errors: EINVAL, ECUDA. */
 BPMF_API int bpmf_set_timing(bpmf_t *h, int enable);
@@ -268,13 +284,16 @@ BPMF_API int bpmf_get_timing(bpmf_t *h, double *ms, int64_t *phase_count, int64_
 BPMF_API int bpmf_hyper_stats_noalloc(const float *X, int64_t R, int32_t K, double *xbar,
                                       double *S, void *stream);
 
-/* Frees the handle and all its device memory.  NULL is ignored. */
+/* Frees the handle and all its device memory (no operation of the paper).
+ * NULL is ignored; never fails. */
 BPMF_API void bpmf_destroy(bpmf_t *h);
 
-/* Static name of a status code. */
+/* Static name of a status code (the caller does not free it). */
 BPMF_API const char *bpmf_strerror(int code);
 
-/* Detail of the last failure on this host thread ("" if none). */
+/* Detail of the last failure on this host thread ("" if none): which call
+ * refused or failed, and why.  The string belongs to the library; a later
+ * call on the same thread may overwrite it. */
 BPMF_API const char *bpmf_last_error(void);
 
 /* ---- job server: continuous batching of independent samplers ----------
