@@ -95,7 +95,9 @@ static void box_muller(uint32_t a, uint32_t b, double *z0, double *z1) {
 
 /* The n standard normals of counter base (c0, c1, ., c3): normal k comes
  * from sub-index k / 4; words (x0, x1) give normals 4q, 4q+1 and (x2, x3)
- * give 4q+2, 4q+3. */
+ * give 4q+2, 4q+3.  The paper only says the draws add random noise
+ * (Algorithm 1) and names the STL generators of its CPU code; the generator
+ * and this layout are the reading both implementations share. */
 void orc_normals(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c3, int64_t n, double *z) {
   for (int64_t q = 0; 4 * q < n; ++q) {
     uint32_t x[4];
@@ -143,7 +145,9 @@ int orc_gamma(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c3, double shape
 /* Dense FP64 linear algebra on row-major K x K matrices                    */
 /* ------------------------------------------------------------------------ */
 
-/* Lower Cholesky factor L (A = L L^T), written to L with a zero upper part. */
+/* Lower Cholesky factor L (A = L L^T), written to L with a zero upper part:
+ * the factorisation behind the K x K inversion of every row update (paper
+ * Sec. IV-B, Fig. 2) and of the Wishart draw. */
 int orc_cholesky(int K, const double *A, double *L) {
   for (int i = 0; i < K * K; ++i) L[i] = 0.0;
   for (int j = 0; j < K; ++j) {
@@ -439,7 +443,9 @@ int orc_sweep(int side, int64_t R, const int64_t *ptr, const int32_t *idx, const
 /* Structure, initialisation and prediction                                 */
 /* ------------------------------------------------------------------------ */
 
-/* Training mean, summed in input order. */
+/* Training mean, summed in input order.  The paper does not state how the
+ * ratings are centred; both implementations subtract this mean and add it
+ * back to predictions. */
 double orc_mean(int64_t n, const float *val) {
   double s = 0.0;
   for (int64_t e = 0; e < n; ++e) s += (double)val[e];
@@ -448,7 +454,8 @@ double orc_mean(int64_t n, const float *val) {
 
 /* Compressed rows of the triples keyed by `key` (users for CSR, movies for
  * CSC) with a stable counting sort: inside a row the triples keep their
- * input order.  Values are centred by `mean`. */
+ * input order.  Values are centred by `mean`.  These are the per-row rating
+ * lists Algorithm 1 walks for every movie and every user. */
 int orc_build_compressed(int64_t nrows, int64_t nnz, const int32_t *key, const int32_t *other,
                          const float *val, double mean, int64_t *ptr, int32_t *idx,
                          double *cval) {
@@ -471,7 +478,8 @@ int orc_build_compressed(int64_t nrows, int64_t nnz, const int32_t *key, const i
 }
 
 /* Rows ordered by degree, largest first, ties by row id (a total order, so
- * the permutation is unique). */
+ * the permutation is unique).  The paper schedules rows by their number of
+ * ratings (Sec. IV-B); this fixes one unique order for the degree bins. */
 static const int64_t *g_deg_ptr;
 static int cmp_deg(const void *pa, const void *pb) {
   int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
@@ -487,7 +495,8 @@ void orc_degree_order(int64_t nrows, const int64_t *ptr, int64_t *perm) {
 }
 
 /* Initial factors: X[i, k] = 0.1 z_k with z the normals of counter base
- * (i, 0, ., INIT << 8 | side). */
+ * (i, 0, ., INIT << 8 | side).  The paper does not state the initial state
+ * of the chain; this small random start is the reading both sides share. */
 void orc_init_factors(int64_t R, int K, uint64_t seed, int side, double *X, int64_t ldx) {
   for (int64_t i = 0; i < R; ++i) {
     orc_normals(seed, (uint32_t)i, 0u, (ORC_STREAM_INIT << 8) | (uint32_t)side, K, X + i * ldx);
