@@ -5,8 +5,10 @@
 // forbids cudaMalloc after start-up, or a runtime that must not synchronise
 // the device (cudaMalloc and cudaFree can).  bpmf_hyper_stats_noalloc gives
 // them the factor-statistics reduction of a side (row mean and centred
-// scatter) with its scratch in a fixed array compiled into this library
-// instead of memory allocated per call.
+// scatter: the sufficient statistics of the Normal-Wishart hyperparameter
+// draw of Algorithm 1, paper Sec. II) with its scratch in a fixed array
+// compiled into this library instead of memory allocated per call.  The
+// entry point itself has no counterpart in the paper.
 //
 // The scratch is one file-scope __device__ array of kScratchDoubles doubles
 // (2 MiB) that every GPU which loads the library holds until the process

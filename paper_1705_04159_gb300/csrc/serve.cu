@@ -1,5 +1,7 @@
 // serve.cu -- a job server over the sampler: continuous batching of many
-// independent BPMF jobs on one GPU.
+// independent BPMF jobs on one GPU.  The paper has no counterpart: it runs
+// one chain (Algorithm 1) across a whole machine; here each job is such a
+// chain, and many of them share one GPU.
 //
 // Jobs are submitted from any host thread (their arrays are copied at
 // submission) and wait in arrival order.  One worker thread owns the GPU
