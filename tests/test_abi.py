@@ -137,3 +137,24 @@ def test_null_handle_is_rejected_with_a_message(libpath, name, args):
     L = bp.lib()
     assert getattr(L, name)(None, *args) == bp.EINVAL
     assert L.bpmf_last_error().decode().startswith(name + ": invalid argument")
+
+
+def test_missing_library_fails_loudly():
+    """Without the built CUDA library every call raises: there is no CPU or
+    eager fallback behind the binding."""
+    code = (
+        "import numpy as np\n"
+        "import paper_1705_04159_gb300 as bp\n"
+        "bp._build.LIB = '/nonexistent/libbpmf_missing.so'\n"
+        "try:\n"
+        "    bp.Sampler(4, 4, np.zeros(1, np.int32), np.zeros(1, np.int32),\n"
+        "               np.ones(1, np.float32), K=2)\n"
+        "except RuntimeError as e:\n"
+        "    assert 'is not built' in str(e), e\n"
+        "    print('raised')\n"
+    )
+    import sys
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == "raised"
