@@ -508,11 +508,14 @@ def reference_arm(args, world, rank):
     K = ds.K
     for _ in range(max(0, min(args.warmup, 1))):
         cpu_oracle_rate(ds, K, min(args.cpu_budget, 5.0), seed=99)
+    # each step a bounded sample: about --cpu-budget seconds, less when many
+    # steps are asked for, so that the whole run stays within a few minutes
+    per_step = min(args.cpu_budget, max(2.0, 150.0 / max(1, args.steps)))
     rates = []
     t0 = time.perf_counter()
     sample = cores = None
     for k in range(args.steps):
-        r, sample, cores, _ = cpu_oracle_rate(ds, K, args.cpu_budget, seed=k)
+        r, sample, cores, _ = cpu_oracle_rate(ds, K, per_step, seed=k)
         rates.append(r)
     elapsed = time.perf_counter() - t0
     value = statistics.mean(rates)
