@@ -92,3 +92,24 @@ def test_bank_model_special_cases():
     # two words 32 floats apart share a bank group: two passes
     assert gen.passes([0, 32]) == 2
     assert gen.passes([0, 32, 64, 4]) == 3
+
+
+def test_table_is_what_the_seeded_generator_writes():
+    """The committed table is reproducible: gen_ws_units.py draws every grid
+    from one seeded random stream in order of g, so rerunning it for the
+    smallest grids (g <= 8, a prefix of that stream) must give the first
+    entries of the table and their round offsets exactly."""
+    import random
+    gmin, _, units, rows = _table()
+    gen = _gen()
+    rng = random.Random(gen.SEED)
+    flat = []
+    for g in range(gen.G_MIN, 9):
+        starts = []
+        for p in range(g):
+            starts.append(len(flat) // 32)
+            lanes, _ = gen.schedule(g, p, rng) if p < g - 1 else ([], 0)
+            flat += lanes
+        starts.append(len(flat) // 32)
+        assert starts == rows[g - gmin][:g + 1], g
+    assert flat == units[:len(flat)]
