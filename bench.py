@@ -42,8 +42,24 @@ if ROOT not in sys.path:
 METRIC = "rows sampled/s per Gibbs sweep"
 UNIT = "rows/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 CUDA-core peak derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (2 flop each per clock)
+# DRAM bytes per launch of the dominant kernel from one ncu capture, with the
+# case and kernel version they were taken on; keyed by (workload, side,
+# heavy kernel, consumer warps).  A capture of a smaller case is scaled to the
+# full launch by ratings (the per-rating index and value reads dominate).
+TRAFFIC = {}
+
+
+def fp32_peak_from(sms, sm_mhz):
+    """FP32 CUDA-core peak in TFLOP/s from unit counts: SMs x 128 lanes x 2 flop x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_mhz):
+    """The same for this device's SM count."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    return fp32_peak_from(sms, sm_mhz), sms
 
 
 def parse():
@@ -70,6 +86,8 @@ def parse():
     p.add_argument("--path", default="mixed", choices=["mixed", "binned", "plain"],
                    help="execution path of the main arm")
     p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    p.add_argument("--no-cpu-full", action="store_true",
+                   help="skip the fully timed oracle iteration of the CPU baseline")
     return p.parse_args()
 
 
@@ -377,6 +395,26 @@ def cpu_oracle_rate(ds, K, budget_s, seed=0):
     return rate, sample, oracle.max_threads(), parts
 
 
+def cpu_oracle_full_iteration(ds, K, seed=0):
+    """One whole Gibbs iteration of the oracle, timed: hyperparameters and every
+    row of the users, the same for the movies, then every test prediction
+    (Algorithm 1's loop body, as oracle.Chain runs it)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    mu = oracle.mean(ds.train_val)
+    csr = oracle.build_compressed(ds.M, ds.train_row, ds.train_col, ds.train_val, mu)
+    csc = oracle.build_compressed(ds.N, ds.train_col, ds.train_row, ds.train_val, mu)
+    U = rng.normal(size=(ds.M, K)) * 0.3
+    V = rng.normal(size=(ds.N, K)) * 0.3
+    prior = dict(mu0=np.zeros(K), beta0=2.0, nu0=float(K), W0=np.eye(K))
+    t0 = time.perf_counter()
+    for side, (X, Xo, (ptr, idx, val)) in enumerate(((U, V, csr), (V, U, csc))):
+        Lam, m = oracle.sample_hyper(X, prior, 0, 0, side)
+        oracle.sweep(side, ptr, idx, val, Xo, Lam, m, ds.alpha, 0, 0, X)
+    oracle.predict(ds.test_row, ds.test_col, U, V, mu)
+    return time.perf_counter() - t0
+
+
 # ----------------------------------------------------------------- main --
 
 def main():
@@ -438,27 +476,34 @@ def main():
     peaks, peak_src = measured_peaks()
     f_gram, f_chol, nbytes = work[side]
     t_ms = per[dom]
-    terms = {"tensor": f_gram / (peaks["bf16_tflops"] * 1e12) * 1e3,
-             "alu": f_chol / (FP32_PEAK_TFLOPS * 1e12) * 1e3,
-             "hbm": nbytes / (peaks["hbm_gbs"] * 1e9) * 1e3}
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak, n_sms = fp32_peak_tflops(sm_mhz)
+    if args.path == "mixed":
+        # the Gram on the tensor cores (bf16), the factorisations on the FP32 lanes
+        terms = {"tensor": f_gram / (peaks["bf16_tflops"] * 1e12) * 1e3,
+                 "alu": f_chol / (fp32_peak * 1e12) * 1e3,
+                 "hbm": nbytes / (peaks["hbm_gbs"] * 1e9) * 1e3}
+    else:
+        # the FP32 paths run the Gram and the factorisations on the FP32 lanes
+        terms = {"alu": (f_gram + f_chol) / (fp32_peak * 1e12) * 1e3,
+                 "hbm": nbytes / (peaks["hbm_gbs"] * 1e9) * 1e3}
     bound = max(terms, key=terms.get)
     if bound == "hbm":
         achieved, peak, unit = nbytes / (t_ms / 1e3) / 1e9, peaks["hbm_gbs"], "GB/s"
     elif bound == "tensor":
         achieved, peak, unit = f_gram / (t_ms / 1e3) / 1e12, peaks["bf16_tflops"], "TFLOP/s"
     else:
-        achieved, peak, unit = f_chol / (t_ms / 1e3) / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s"
-    # DRAM bytes per launch from one ncu capture of the persistent row kernel
-    # on the 120k-user, 18M-rating case (users launch: 166.3 MB read + 28.1 MB
-    # written), scaled to the full launch by ratings (x5: the per-rating index
-    # and value reads dominate)
-    traffic = (166.3e6 + 28.1e6) * 5 if (args.workload == "netflix" and side == 0 and
-                                          mixed["thresholds"][0][3] == 1) else None
+        flops = f_chol if args.path == "mixed" else f_gram + f_chol
+        achieved, peak, unit = flops / (t_ms / 1e3) / 1e12, fp32_peak, "TFLOP/s"
+    key = (args.workload, side, mixed["thresholds"][side][3], mixed["thresholds"][side][4])
+    traffic, traffic_note = TRAFFIC.get(key, (None, "no ncu capture of this kernel version"))
     roofline = {"kernel": f"row update, {'users' if side == 0 else 'movies'} side",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_note": (f"alu: FP32 CUDA-core peak from unit counts (152 SMs x 128 lanes x 2 x "
-                              f"2.07 GHz); tensor and hbm {peak_src} (bf16 burst, copy)"),
+                "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                "peak_note": (f"alu: FP32 CUDA-core peak from unit counts ({n_sms} SMs x "
+                              f"{FP32_LANES_PER_SM} lanes x 2 flop x {sm_mhz:.0f} MHz, the median "
+                              f"SM clock sampled under load); tensor and hbm {peak_src} "
+                              f"(bf16 burst, copy)"),
                 "roofline_ms": terms, "ms_per_launch": t_ms,
                 "gram_flops_per_launch": f_gram, "chol_flops_per_launch": f_chol,
                 "algorithmic_bytes_per_launch": nbytes}
@@ -471,12 +516,23 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, cores, parts = cpu_oracle_rate(ds, K, args.cpu_budget)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        if not args.no_cpu_full:
+            t_full = cpu_oracle_full_iteration(ds, K)
+            cpu["full_iteration"] = {"s": t_full, "value": (ds.M + ds.N) / t_full,
+                                     "what": "one whole iteration timed: both hyper draws, every "
+                                             "row of both sides, every test prediction"}
+            cpu["value"] = (ds.M + ds.N) / t_full
+            cpu["sample"] = ("one whole iteration of the workload, timed (the bounded-sample "
+                             f"estimate beside it: {rate:.4g} rows/s from {sample})")
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32 (Gram of heavy rows: bf16 hi/lo split, 3 tensor-core products, f32 "
+                      "accumulation; Cholesky and solves f32; FP64 redo of flagged rows)"
+                      if args.path == "mixed" else "f32"),
             "data": f"synthetic (seeded {ds.name}-shaped ratings generated on the device)",
             "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train + "
                                    f"{len(ds.test_row)} test ratings, K={K}",
@@ -500,34 +556,90 @@ def main():
         dist.destroy_process_group()
 
 
+class OracleSteps:
+    """Bounded steps of the oracle on one workload.  A step draws both sides'
+    hyperparameters from all their rows, redraws n_users random users and
+    n_movies random movies, and predicts n_test random test pairs; it counts
+    the rows it redrew.  The compressed structure is built once, outside the
+    steps (it is the initialisation, not part of an iteration)."""
+
+    def __init__(self, ds, K):
+        import oracle
+        self.o, self.ds, self.K = oracle, ds, K
+        self.mu = oracle.mean(ds.train_val)
+        self.csr = oracle.build_compressed(ds.M, ds.train_row, ds.train_col, ds.train_val,
+                                           self.mu)
+        self.csc = oracle.build_compressed(ds.N, ds.train_col, ds.train_row, ds.train_val,
+                                           self.mu)
+        rng = np.random.default_rng(1)
+        self.U = rng.normal(size=(ds.M, K)) * 0.3
+        self.V = rng.normal(size=(ds.N, K)) * 0.3
+        self.prior = dict(mu0=np.zeros(K), beta0=2.0, nu0=float(K), W0=np.eye(K))
+
+    def sizes(self, frac):
+        """Row and test-pair counts of a step covering `frac` of an iteration."""
+        ds = self.ds
+        return (max(1, int(ds.M * frac)), max(1, int(ds.N * frac)),
+                max(1, int(len(ds.test_row) * frac)) if len(ds.test_row) else 0)
+
+    def step(self, frac, seed):
+        """(seconds, rows redrawn) of one step covering `frac` of an iteration."""
+        o, ds = self.o, self.ds
+        n_u, n_v, n_t = self.sizes(frac)
+        rng = np.random.default_rng(seed)
+        subs = (rng.choice(ds.M, size=n_u, replace=False),
+                rng.choice(ds.N, size=n_v, replace=False))
+        tsel = rng.choice(len(ds.test_row), size=n_t, replace=False) if n_t else None
+        t0 = time.perf_counter()
+        for side, (X, Xo, (ptr, idx, val)) in enumerate(((self.U, self.V, self.csr),
+                                                         (self.V, self.U, self.csc))):
+            Lam, m = o.sample_hyper(X, self.prior, 0, seed, side)
+            o.sweep(side, ptr, idx, val, Xo, Lam, m, ds.alpha, 0, seed, X, subset=subs[side])
+        if n_t:
+            o.predict(ds.test_row[tsel], ds.test_col[tsel], self.U, self.V, self.mu)
+        return time.perf_counter() - t0, n_u + n_v
+
+
 def reference_arm(args, world, rank):
-    """The FP64 CPU oracle as the reference arm, on bounded samples."""
+    """The FP64 CPU oracle as the reference arm.  Every step is a bounded
+    sample of one iteration of the workload (OracleSteps), timed as it runs:
+    ms_per_step is the measured time of a step and value the rows it redrew
+    per second, so ms_per_step x steps is the timed part of the run."""
     if rank != 0:
         return
     ds = load_workload(args.workload, args.seed, "cuda" if _cuda() else "cpu")
     K = ds.K
-    for _ in range(max(0, min(args.warmup, 1))):
-        cpu_oracle_rate(ds, K, min(args.cpu_budget, 5.0), seed=99)
-    # each step a bounded sample: about --cpu-budget seconds, less when many
-    # steps are asked for, so that the whole run stays within a few minutes
+    steps = OracleSteps(ds, K)
+    # the fraction of an iteration one step covers: about --cpu-budget seconds
+    # (less when many steps are asked for, so that the run stays within a few
+    # minutes), sized from a short calibration step
     per_step = min(args.cpu_budget, max(2.0, 150.0 / max(1, args.steps)))
-    rates = []
+    f = min(1.0, 200.0 / max(1, ds.M + ds.N))
+    t, _ = steps.step(f, seed=997)
+    f = min(1.0, f * max(1.0, per_step / max(t, 1e-3)))
+    for w in range(args.warmup):
+        steps.step(f, seed=1000 + w)
+    times, rows = [], 0
     t0 = time.perf_counter()
-    sample = cores = None
     for k in range(args.steps):
-        r, sample, cores, _ = cpu_oracle_rate(ds, K, per_step, seed=k)
-        rates.append(r)
+        dt, n = steps.step(f, seed=k)
+        times.append(dt)
+        rows += n
     elapsed = time.perf_counter() - t0
-    value = statistics.mean(rates)
-    ms = (ds.M + ds.N) / value * 1e3
+    value = rows / sum(times)
+    n_u, n_v, n_t = steps.sizes(f)
+    import oracle
+    sample = (f"each step: hyper draws of both sides on all rows, row draws of {n_u} random users "
+              f"and {n_v} random movies, predictions of {n_t} random test pairs "
+              f"({f:.3%} of an iteration's rows); value = rows redrawn / step seconds")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": f"synthetic (seeded {ds.name}-shaped ratings)",
             "config": {"workload": f"{ds.name}: {ds.M}x{ds.N}, {ds.nnz} train ratings, K={K}",
-                       "global_batch": ds.M + ds.N, "parallelism": "host cores"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                       "global_batch": n_u + n_v, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": elapsed}
     print(json.dumps(line))

@@ -86,8 +86,10 @@ typedef struct {
   uint64_t seed;      /* Philox key */
   int32_t order;      /* 0: users then movies in an iteration; 1: movies then users */
   int32_t burnin;     /* iterations before the running mean of predictions starts */
-  int32_t light_max;  /* rows with degree <= light_max take the FP32 CTA kernel on the MIXED
-                         path (heavier rows the tensor-core kernel); -1: automatic */
+  int32_t light_max;  /* rows with degree <= light_max take the FP32 light-row kernel on the
+                         BINNED and MIXED paths (one warp per row for K <= 32, else one CTA
+                         per row); heavier rows take the heavy-row kernel (tensor-core Gram
+                         on MIXED, FP32 CTA per row on BINNED); -1: automatic */
   int32_t hub_min;    /* rows with degree >= hub_min are split across CTAs; -1: automatic */
   int32_t tiny_max;   /* rows with degree <= tiny_max take the rank-one kernel (BINNED and
                          MIXED paths); -1: automatic */
@@ -99,12 +101,18 @@ typedef struct {
                          split threshold by hand); the choice is remembered for the process
                          per (device, K, path, side shape, degree histogram in powers of
                          two); 0: fixed defaults */
+  double pivot_rel;   /* FP32 accuracy guard of the row draws, in [0, 1): a row whose FP32
+                         Cholesky meets a pivot at or below pivot_rel times its column's
+                         starting diagonal (Lambda*_kk) is redrawn from scratch in FP64.
+                         The pivot ratio of column k is 1 / (Lambda*_kk (A_k^-1)_kk) for the
+                         leading block A_k, a lower bound on how far the row's conditioning
+                         lets FP32 drift; 0 flags only pivots <= 0.  Default 3e-2 */
 } bpmf_config;
 
 /* Fills `cfg` with the defaults: path MIXED, alpha 2, beta0 2, nu0 K,
  * mu0 = 0, W0 = I, seed 0, order 0, burnin 0, automatic thresholds,
  * autotune 0 (fixed defaults: the kernel choice, hence the FP32 rounding of
- * every draw, does not depend on timings). */
+ * every draw, does not depend on timings), pivot_rel 3e-2. */
 BPMF_API void bpmf_config_default(bpmf_config *cfg, int32_t K);
 
 /* Creates a sampler for the M x N training ratings given as nnz triples
@@ -115,7 +123,10 @@ BPMF_API void bpmf_config_default(bpmf_config *cfg, int32_t K);
  * stable sort (a row's ratings keep their input order), orders each side's
  * rows by degree, and initialises U and V to 0.1 z (Philox stream 4).
  * `stream` is a cudaStream_t (NULL: legacy default stream).
- * Errors: EINVAL (shape, index, K, prior not SPD), ENOMEM, ECUDA. */
+ * alpha, beta0 and nu0 must be finite, pivot_rel finite in [0, 1), and every
+ * rating finite.
+ * Errors: EINVAL (shape, index, non-finite value, K, prior not SPD), ENOMEM,
+ * ECUDA. */
 BPMF_API int bpmf_init(bpmf_t **out, int64_t M, int64_t N, int64_t nnz, const int32_t *row,
               const int32_t *col, const float *val, const bpmf_config *cfg, void *stream,
               uint32_t flags);
@@ -123,7 +134,7 @@ BPMF_API int bpmf_init(bpmf_t **out, int64_t M, int64_t N, int64_t nnz, const in
 /* Registers n held-out test triples (Algorithm 1, "for all test points").
  * After it, each bpmf_step predicts them and keeps the running mean of the
  * predictions from iteration `burnin` on.  Replaces any earlier test set.
- * Errors: EINVAL (index out of range), ENOMEM, ECUDA. */
+ * Errors: EINVAL (index out of range, non-finite rating), ENOMEM, ECUDA. */
 BPMF_API int bpmf_set_test(bpmf_t *h, int64_t n, const int32_t *row, const int32_t *col,
                   const float *val, uint32_t flags);
 
@@ -212,8 +223,9 @@ BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
 
 /* Work counters of `side`: rows per degree bin [tiny, light, heavy, hub]
  * (tiny: degree <= tiny_max, rank-one updates of chol(Lambda_s), one warp
- * per row; light: degree <= light_max, FP32 Gram, one CTA per row; heavy:
- * tensor-core Gram on the MIXED path; hub: degree >= hub_min, split across
+ * per row; light: degree <= light_max, FP32 Gram, one warp per row for
+ * K <= 32, else one CTA per row; heavy: tensor-core Gram on the MIXED path,
+ * FP32 CTA per row on BINNED; hub: degree >= hub_min, split across
  * CTAs) and the number of rows the last sweep redid in FP64 (paper Sec. IV-B:
  * a cheap kernel for rows with few ratings, split tasks for rows with many).
  * Errors: EINVAL. */
@@ -242,6 +254,22 @@ BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[5]);
  * changes which kernel draws a row, not the conditional it draws from.
  * Errors: EINVAL (nothing changed), ECUDA. */
 BPMF_API int bpmf_set_thresholds(bpmf_t *h, int side, const int64_t thresholds[5]);
+
+/* Failure-path limits (the paper has no counterpart; both default to values
+ * that normal runs never reach, and lowering them is how the failure paths
+ * are exercised without faulting anything).
+ *  - gamma_cap: Marsaglia-Tsang attempts allowed per Gamma draw of the
+ *    Wishart step (0..64; negative: the default 64).  A draw that needs more
+ *    attempts makes bpmf_sample_hyper (and bpmf_step) return BPMF_ERNG; with
+ *    0 every draw does.  Draws that succeed are the same at any cap.
+ *  - wait_ns: bound in nanoseconds on each wait between the roles of the
+ *    persistent row kernel (>= 1; 0 or negative: the default 2 s).  A wait
+ *    that runs out makes every role of the kernel leave its loop, wait for its
+ *    own copies and tensor-core work in flight and free its tensor memory;
+ *    the call then returns BPMF_ECUDA with "timed out" in bpmf_last_error, the
+ *    rows of that sweep are undefined, and the handle stays usable.
+ * The next bpmf_step re-records its graph.  Errors: EINVAL. */
+BPMF_API int bpmf_set_limits(bpmf_t *h, int32_t gamma_cap, int64_t wait_ns);
 
 /* ---- kernel timers (bpmf_get_timing) ---- */
 #define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */

@@ -60,7 +60,7 @@ class Config(C.Structure):
         ("nu0", C.c_double), ("mu0", C.c_void_p), ("W0", C.c_void_p), ("seed", C.c_uint64),
         ("order", C.c_int32), ("burnin", C.c_int32), ("light_max", C.c_int32),
         ("hub_min", C.c_int32), ("tiny_max", C.c_int32), ("heavy_kernel", C.c_int32),
-        ("autotune", C.c_int32),
+        ("autotune", C.c_int32), ("pivot_rel", C.c_double),
     ]
 
 
@@ -122,6 +122,7 @@ def lib():
         L.bpmf_get_sweep_info.argtypes = [P, C.c_int, P, P]
         L.bpmf_set_timing.argtypes = [P, C.c_int]
         L.bpmf_set_graph.argtypes = [P, C.c_int]
+        L.bpmf_set_limits.argtypes = [P, i32, i64]
         L.bpmf_get_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_set_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
@@ -336,6 +337,12 @@ def bpmf_set_graph(h, enable=True):
     _check(lib().bpmf_set_graph(h, 1 if enable else 0), "bpmf_set_graph")
 
 
+def bpmf_set_limits(h, gamma_cap=-1, wait_ns=0):
+    """Failure-path limits: Gamma attempts per draw (negative: default 64) and
+    the bound of each persistent-kernel wait in ns (0: default 2 s)."""
+    _check(lib().bpmf_set_limits(h, int(gamma_cap), int(wait_ns)), "bpmf_set_limits")
+
+
 def bpmf_get_timing(h):
     """({timer: ms}, {timer: phases}, kernels launched) since timing was enabled."""
     ms = np.zeros(len(TIMERS))
@@ -346,17 +353,36 @@ def bpmf_get_timing(h):
     return dict(zip(TIMERS, ms.tolist())), dict(zip(TIMERS, cnt.tolist())), k.value
 
 
+def _check_noalloc_args(X, R, K, xbar, S):
+    """Argument checks of bpmf_hyper_stats_noalloc that the C call cannot make
+    (it sees bare pointers): device tensors on one device, each large enough
+    for R x K, K and K x K elements.  Raises TypeError or ValueError."""
+    if not (_is_cuda_tensor(X) and _is_cuda_tensor(xbar) and _is_cuda_tensor(S)):
+        raise TypeError("bpmf_hyper_stats_noalloc takes device tensors only")
+    if not (X.device == xbar.device == S.device):
+        raise ValueError("bpmf_hyper_stats_noalloc: X, xbar and S must be on one device")
+    R, K = int(R), int(K)
+    if R < 1 or K < 1:
+        raise ValueError("bpmf_hyper_stats_noalloc: R and K must be positive")
+    if X.numel() < R * K or xbar.numel() < K or S.numel() < K * K:
+        raise ValueError(f"bpmf_hyper_stats_noalloc: buffers too small for R={R}, K={K} "
+                         f"(X {X.numel()}, xbar {xbar.numel()}, S {S.numel()} elements)")
+
+
 def bpmf_hyper_stats_noalloc(X, R, K, xbar, S, stream=None):
     """Row mean and centred scatter of the device factor matrix X (R x K float32)
     into the device tensors xbar (K float64) and S (K*K float64), with no
-    allocation (scratch compiled into the library; see include/bpmf.h)."""
-    px, kx, dx = _ptr(X, np.float32)
-    pm, km, dm = _ptr(xbar, np.float64)
-    ps, ks, ds_ = _ptr(S, np.float64)
-    if not (dx and dm and ds_):
-        raise TypeError("bpmf_hyper_stats_noalloc takes device tensors only")
-    _check(lib().bpmf_hyper_stats_noalloc(px, int(R), int(K), pm, ps, _stream_ptr(stream)),
-           "bpmf_hyper_stats_noalloc")
+    allocation (scratch compiled into the library; see include/bpmf.h).  The
+    call runs with X's device current, on `stream` (default: that device's
+    current stream)."""
+    _check_noalloc_args(X, R, K, xbar, S)
+    import torch
+    with torch.cuda.device(X.device):
+        px, kx, _ = _ptr(X, np.float32)
+        pm, km, _ = _ptr(xbar, np.float64)
+        ps, ks, _ = _ptr(S, np.float64)
+        _check(lib().bpmf_hyper_stats_noalloc(px, int(R), int(K), pm, ps, _stream_ptr(stream)),
+               "bpmf_hyper_stats_noalloc")
 
 
 def bpmf_destroy(h):
@@ -416,7 +442,7 @@ class Sampler:
 
     def __init__(self, M, N, row, col, val, K, alpha=2.0, beta0=2.0, nu0=None, mu0=None, W0=None,
                  seed=0, path=PATH_MIXED, order=0, burnin=0, light_max=-1, hub_min=-1,
-                 tiny_max=-1, heavy_kernel=0, autotune=0, stream=None):
+                 tiny_max=-1, heavy_kernel=0, autotune=0, stream=None, pivot_rel=None):
         cfg = bpmf_config_default(K)
         cfg.alpha = float(alpha)
         cfg.beta0 = float(beta0)
@@ -430,6 +456,8 @@ class Sampler:
         cfg.tiny_max = int(tiny_max)
         cfg.heavy_kernel = int(heavy_kernel)
         cfg.autotune = int(autotune)
+        if pivot_rel is not None:
+            cfg.pivot_rel = float(pivot_rel)
         self.M, self.N, self.K = int(M), int(N), int(K)
         self.nnz = int(len(row))
         self.h = bpmf_init(M, N, row, col, val, cfg, stream=stream, mu0=mu0, W0=W0)
@@ -493,6 +521,9 @@ class Sampler:
 
     def set_graph(self, enable=True):
         bpmf_set_graph(self.h, enable)
+
+    def set_limits(self, gamma_cap=-1, wait_ns=0):
+        bpmf_set_limits(self.h, gamma_cap, wait_ns)
 
     def thresholds(self, side):
         return bpmf_get_thresholds(self.h, side)

@@ -103,6 +103,10 @@ int check_status(Handle* h, const char* where) {
     set_error("%s: a tensor-core pipeline wait timed out", where);
     return BPMF_ECUDA;
   }
+  if (st & kStatusValue) {
+    set_error("%s: an input value is not finite", where);
+    return BPMF_EINVAL;
+  }
   return BPMF_OK;
 }
 
@@ -255,6 +259,7 @@ void bpmf_config_default(bpmf_config* c, int32_t K) {
   c->tiny_max = -1;
   c->heavy_kernel = 0;
   c->autotune = 0;
+  c->pivot_rel = 3e-2;
 }
 
 const char* bpmf_strerror(int code) {
@@ -285,7 +290,9 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
   const int K = cfg->K;
   if (K < 1 || K > kMaxK || M < 1 || N < 1 || M >= (1LL << 31) || N >= (1LL << 31) || nnz < 0 ||
       nnz >= (1LL << 31) || (nnz > 0 && (!row || !col || !val)) || !(cfg->alpha > 0.0) ||
-      !(cfg->beta0 > 0.0) || !(cfg->nu0 > (double)K - 1.0) || cfg->path < BPMF_PATH_PLAIN ||
+      !isfinite(cfg->alpha) || !(cfg->beta0 > 0.0) || !isfinite(cfg->beta0) ||
+      !(cfg->nu0 > (double)K - 1.0) || !isfinite(cfg->nu0) || !(cfg->pivot_rel >= 0.0) ||
+      !(cfg->pivot_rel < 1.0) || cfg->path < BPMF_PATH_PLAIN ||
       cfg->path > BPMF_PATH_MIXED || (cfg->order != 0 && cfg->order != 1) || cfg->burnin < 0 ||
       cfg->heavy_kernel < 0 || cfg->heavy_kernel > 2) {
     set_error("bpmf_init: invalid shape or configuration (K=%d M=%lld N=%lld nnz=%lld)", K,
@@ -507,6 +514,15 @@ int bpmf_step(bpmf_t* hh) {
   const int rc = check_status(h, "bpmf_step");
   if (rc == BPMF_OK && h->use_graph && h->timing) BPMF_TRY(resolve_graph_timers(h));
   return rc;
+}
+
+int bpmf_set_limits(bpmf_t* hh, int32_t gamma_cap, int64_t wait_ns) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || gamma_cap > kGammaCap) return einval("bpmf_set_limits");
+  drop_graph(h);  // the captured iteration holds the old limits
+  h->gamma_cap = gamma_cap < 0 ? kGammaCap : gamma_cap;
+  h->wait_ns = wait_ns > 0 ? (uint64_t)wait_ns : kWaitNsDefault;
+  return BPMF_OK;
 }
 
 int bpmf_set_graph(bpmf_t* hh, int enable) {

@@ -12,7 +12,8 @@
 //         hub sums its partials in piece order (deterministic) and factorises;
 //   heavy (light_max < degree < hub_min): one CTA per row, tensor-core Gram
 //         on the MIXED path, FP32 Gram otherwise;
-//   light (tiny_max < degree <= light_max): one CTA per row, FP32 Gram;
+//   light (tiny_max < degree <= light_max): FP32 Gram; one warp per row for
+//         K <= 32 (rows_warp.cu), else one CTA per row;
 //   tiny  (degree <= tiny_max, degree 0 included): one warp per row, rank-one
 //         updates of chol(Lambda_s) (rank1.cu).
 // The thresholds are fixed by the configuration, or by defaults, or -- with
@@ -60,7 +61,15 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
       BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
     r.row_begin = e_heavy;
     r.row_end = e_light;
+    if (warp_supported(h->K)) BPMF_TRY(launch_rows_warp(r, st, &h->kernels));
+    else BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
+  } else if (warp_supported(h->K)) {
+    r.row_begin = e_hub;
+    r.row_end = e_heavy;
     BPMF_TRY(launch_rows_fp32(r, st, &h->kernels));
+    r.row_begin = e_heavy;
+    r.row_end = e_light;
+    BPMF_TRY(launch_rows_warp(r, st, &h->kernels));
   } else {
     r.row_begin = e_hub;
     r.row_end = e_light;
@@ -356,10 +365,14 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     }
     BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, best_v));
   }
-  if (h->cfg.light_max < 0 && h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K)) {
+  const bool light_differs =
+      (h->cfg.path == BPMF_PATH_MIXED && (tc_supported(h->K) || (ws_supported(h->K) && sd.Xhi))) ||
+      (h->cfg.path == BPMF_PATH_BINNED && warp_supported(h->K));
+  if (h->cfg.light_max < 0 && light_differs) {
     int64_t best_v = sd.light_max;
     float best = 3.0e38f;
-    for (int64_t v : distinct_cuts(sd, {sd.tiny_max, 8, 16, 32, 64, 128, 256, 512, 1024})) {
+    for (int64_t v : distinct_cuts(sd, {sd.tiny_max, 8, 16, 32, 64, 128, 256, 512, 1024, 4096,
+                                        (int64_t)1 << 40})) {
       if (v < sd.tiny_max) continue;
       BPMF_TRY(apply_bins(h, s, sd.tiny_max, v, sd.hub_min));
       BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));

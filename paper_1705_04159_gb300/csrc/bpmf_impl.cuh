@@ -19,7 +19,8 @@
 namespace gb {
 
 constexpr int kMaxK = 128;
-constexpr int kGammaCap = 64;
+constexpr int kGammaCap = 64;                   // Gamma rejection attempts per draw
+constexpr uint64_t kWaitNsDefault = 2000000000ull;  // 2 s bound per pipeline wait
 
 // Philox stream ids (high word of the counter's last element)
 constexpr uint32_t kStreamRow = 0u;
@@ -33,6 +34,7 @@ constexpr int kStatusNotPD = 1;
 constexpr int kStatusRng = 2;
 constexpr int kStatusIndex = 4;
 constexpr int kStatusTimeout = 8;  // a bounded wait on the tensor-core pipeline gave up
+constexpr int kStatusValue = 16;   // an input rating is not finite
 
 // degree bins
 enum Bin { kBinTiny = 0, kBinLight = 1, kBinHeavy = 2, kBinHub = 3, kNumBins = 4 };
@@ -129,6 +131,9 @@ struct Handle {
   double t_ms[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
   int64_t t_cnt[BPMF_NUM_TIMERS] = {0, 0, 0, 0, 0, 0};
   int64_t kernels = 0;
+  // failure-path limits (bpmf_set_limits)
+  int gamma_cap = kGammaCap;
+  uint64_t wait_ns = kWaitNsDefault;
 };
 
 // Brackets one phase with two events when timing is on (api.cu).

@@ -124,6 +124,25 @@ __global__ void __launch_bounds__(256, 2) scatter_partial(const float* __restric
     stash(0);
   }
   __syncthreads();
+  // the FP32 sums are moved into this block's FP64 partial every kFlushChunks
+  // chunks, so that no FP32 accumulator sums more than 1024 rows however few
+  // blocks share the rows
+  constexpr int kFlushChunks = 64;
+  double* out = part + (int64_t)blockIdx.x * K * K;
+  int flushed = 0;  // 0: the partial is not written yet
+  auto flush = [&]() {
+    if (!active) return;
+#pragma unroll
+    for (int p = 0; p < TM; ++p)
+#pragma unroll
+      for (int q = 0; q < TM; ++q) {
+        const int i = ty * TM + p, j = tx * TM + q;
+        if (i < K && j < K && j <= i)
+          out[i * K + j] = flushed ? out[i * K + j] + (double)acc[p][q] : (double)acc[p][q];
+        acc[p][q] = 0.f;
+      }
+  };
+  int nchunk = 0;
   for (int64_t c0 = r0; c0 < r1; c0 += CH) {
     const int cnt = (int)min((int64_t)CH, r1 - c0);
     const bool more = c0 + CH < r1;
@@ -145,17 +164,13 @@ __global__ void __launch_bounds__(256, 2) scatter_partial(const float* __restric
     if (more) stash(buf ^ 1);
     __syncthreads();
     buf ^= 1;
+    if (++nchunk == kFlushChunks && more) {
+      flush();
+      flushed = 1;
+      nchunk = 0;
+    }
   }
-  if (active) {
-    double* out = part + (int64_t)blockIdx.x * K * K;
-#pragma unroll
-    for (int p = 0; p < TM; ++p)
-#pragma unroll
-      for (int q = 0; q < TM; ++q) {
-        const int i = ty * TM + p, j = tx * TM + q;
-        if (i < K && j < K && j <= i) out[i * K + j] = (double)acc[p][q];
-      }
-  }
+  flush();
 }
 
 __global__ void scatter_final(const double* __restrict__ part, int blocks, int K,
@@ -298,7 +313,7 @@ __device__ void cta_ata(const double* A, double* C, int K) {
 // a, GAMMA)); the acceptance test decides which attempt is kept, so it runs
 // in FP64 like the reference.  The attempt cap flags kStatusRng.
 __device__ void cta_bartlett_A(double* A, int K, double nu, uint2 key, uint32_t t, int side,
-                               int* status) {
+                               int cap, int* status) {
   const uint32_t sw_w = stream_word(kStreamWishart, side);
   const uint32_t sw_g = stream_word(kStreamGamma, side);
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
@@ -314,7 +329,7 @@ __device__ void cta_bartlett_A(double* A, int K, double nu, uint2 key, uint32_t 
     const double d = s - 1.0 / 3.0;
     const double c = 1.0 / sqrt(9.0 * d);
     double g = -1.0;
-    for (int a = 0; a < kGammaCap && g < 0.0; ++a) {
+    for (int a = 0; a < cap && g < 0.0; ++a) {
       const uint4 w = philox(make_uint4((uint32_t)k, t, (uint32_t)a, sw_g), key);
       double zn, zs;
       normal2_f64(w.x, w.y, zn, zs);
@@ -369,6 +384,7 @@ struct HyperArgs {
   float* lamaug;
   float* lchol;  // chol(Lambda) = B in FP32, packed by rows, for the rank-one row kernel
   int* status;
+  int gamma_cap;  // Gamma rejection attempts per draw before kStatusRng
 };
 
 // The posterior draw.  Two exact identities keep the FP64 work to about
@@ -413,7 +429,7 @@ __global__ void __launch_bounds__(512) wishart_factor(HyperArgs a) {
     }
     return;
   }
-  cta_bartlett_A(A, K, nu_s, seed_key(a.seed), *a.tp, a.side, a.status);
+  cta_bartlett_A(A, K, nu_s, seed_key(a.seed), *a.tp, a.side, a.gamma_cap, a.status);
   if (threadIdx.x == 0) *ok = 1.0;
 }
 
@@ -564,6 +580,7 @@ int launch_hyper(Handle* h, int s) {
   a.lamaug = sd.lamaug;
   a.lchol = sd.lchol;
   a.status = h->status;
+  a.gamma_cap = h->gamma_cap;
   {
     PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
     wishart_factor<<<1, 512, 0, st>>>(a);

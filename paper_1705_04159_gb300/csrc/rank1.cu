@@ -11,6 +11,9 @@
 //   r = sqrt(L_kk^2 + x_k^2), c = r / L_kk, s = x_k / L_kk, L_kk = r,
 //   L_ik = (L_ik + s x_i) / c, x_i = c x_i - s L_ik   (i > k).
 // Then b = Lambda_s mu_s + alpha sum_j r_ij v_j, y = L^-1 b, u = L^-T (y + z).
+// The pivots only grow, so the factorisation never breaks down; a row whose
+// final L_kk^2 is small against Lambda*_kk (the pivot rule of the other row
+// kernels) is still left to the FP64 redo, as FP32 may have lost its digits.
 //
 // One warp per row.  L lives in shared memory packed by rows (element (i, k)
 // at i (i + 1) / 2 + k): the column walks of the update touch one element per
@@ -117,10 +120,14 @@ __global__ void __launch_bounds__(256, 2)
   // b0 = Lambda_s mu_s is the last row of the bordered hyper matrix
   const float* b0 = a.lamaug + (int64_t)K * (K + 1);
   float b[NPL];
+  // starting diagonal Lambda*_ii = (Lambda_s)_ii + alpha sum_j v_ji^2 of the
+  // owned rows, for the pivot rule
+  float d0[NPL];
 #pragma unroll
   for (int m = 0; m < NPL; ++m) {
     const int i = lane + 32 * m;
     b[m] = i < K ? __ldg(b0 + i) : 0.f;
+    d0[m] = i < K ? __ldg(a.lamaug + (int64_t)i * (K + 1) + i) : 0.f;
   }
   __syncwarp();
   const float sa = sqrtf(a.alpha);
@@ -140,16 +147,27 @@ __global__ void __launch_bounds__(256, 2)
         const float v = (live && i < K) ? __ldg(vj + i) : 0.f;
         x[u][m] = sa * v;
         b[m] = fmaf(ar, v, b[m]);
+        d0[m] = fmaf(x[u][m], x[u][m], d0[m]);
       }
     }
     rank_one_wave<NPL>(L, K, x, W, lane);
   }
-  // reciprocal diagonal of the owned rows
+  // reciprocal diagonal of the owned rows; the final L_ii^2 is the pivot a
+  // direct factorisation of Lambda* would meet at column i, so the pivot rule
+  // of the other row kernels applies to it unchanged: a row failing it is
+  // left to the FP64 redo
   float rd[NPL];
+  bool bad = false;
 #pragma unroll
   for (int m = 0; m < NPL; ++m) {
     const int i = lane + 32 * m;
-    rd[m] = i < K ? 1.0f / L[tri(i) + i] : 0.f;
+    const float lii = i < K ? L[tri(i) + i] : 1.f;
+    rd[m] = i < K ? 1.0f / lii : 0.f;
+    if (i < K && !(lii * lii > a.pivot_rel * d0[m])) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
+    return;
   }
   // y = L^-1 b, by columns
   for (int k = 0; k < K; ++k) {

@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(160) row_fp32(const SweepArgs a, int mode) {
   }
   form_bordered<TM>(acc, active, ty, tx, G, a.lamaug, a.alpha, s.diag0);
   __syncthreads();
-  if (!chol_solve_write<TM>(acc, active, ty, tx, G, s, &fail_sh, a.X + (int64_t)row * a.K)) {
+  if (!chol_solve_write<TM>(acc, active, ty, tx, G, s, a.pivot_rel, &fail_sh,
+                           a.X + (int64_t)row * a.K)) {
     if (tid == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;
   }
 }
@@ -360,6 +361,8 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.sw = stream_word(kStreamRow, s);
   a.flag_rows = h->flag_rows;
   a.flag_count = h->flag_count;
+  a.pivot_rel = (float)h->cfg.pivot_rel;
+  a.wait_ns = h->wait_ns;
   a.piece_row = sd.piece_row;
   a.piece_e0 = sd.piece_e0;
   a.piece_e1 = sd.piece_e1;

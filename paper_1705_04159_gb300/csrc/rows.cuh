@@ -26,6 +26,8 @@ struct SweepArgs {
   uint32_t sw;          // stream word (ROW << 8 | side)
   int32_t* flag_rows;   // rows whose FP32 pivot failed
   int32_t* flag_count;
+  float pivot_rel;      // a pivot <= pivot_rel x its starting diagonal flags the row
+  uint64_t wait_ns;     // bound of each pipeline wait of the persistent kernel
   // split rows: piece p covers ratings [piece_e0[p], piece_e1[p]) of piece_row[p];
   // hub h (slot h of the degree order) owns pieces [hub_piece0[h], hub_piece0[h+1])
   const int32_t* piece_row;
@@ -63,6 +65,9 @@ int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* count
                    cudaStream_t st, int64_t* launches);
 // neighbours per stage of the persistent kernel for a side with nnz ratings over R rows
 int ws_stage_neighbours(int64_t nnz, int64_t R);
+// rows row_begin..row_end, one warp per row, FP32 (rows_warp.cu); 1 <= K <= 32
+bool warp_supported(int K);
+int launch_rows_warp(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
 int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
 

@@ -298,7 +298,7 @@ __device__ __forceinline__ void tc_form(const SweepArgs& a, const TileGeom& G, c
 // s.Lr (row stride LDS) and 1 / L_kk to s.rinv.  Returns false on a pivot
 // failure or a wait timeout (flags tell which).
 __device__ __forceinline__ bool tc_cholesky(const TileGeom& G, const TcSmem& s, uint32_t tmem, uint32_t trow,
-                                            int N) {
+                                            int N, float prel) {
   const int K = G.K, KA = G.KA, LDS = G.LDS;
   const int m = threadIdx.x, warp = m >> 5, lane = m & 31;
   const int npanel = (K + 15) / 16;
@@ -321,9 +321,9 @@ __device__ __forceinline__ bool tc_cholesky(const TileGeom& G, const TcSmem& s, 
         const bool live = j < nc;
         float piv = __shfl_sync(0xffffffffu, v[j], b0 + j);
         const float d0 = s.diag0[c0 + (live ? j : 0)];
-        if (live && !(piv > kPivotRel * d0)) {
+        if (live && (!(piv > prel * d0) || !(piv > 0.f))) {
           if (lane == b0 + j) s.flags[0] = 1;
-          piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+          piv = pivot_stand_in(piv, d0);
         }
         piv = live ? piv : 1.0f;
         const float rd = rsqrtf(piv);
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kTcThreads) row_tc(const SweepArgs a, int* sta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    ok = tc_cholesky(G, s, tmem, trow, N);
+    ok = tc_cholesky(G, s, tmem, trow, N, a.pivot_rel);
   }
   tc_release(s, tmem);
   if (s.flags[1]) {

@@ -64,7 +64,6 @@ constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (see trow)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
 constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound (final MMA wait)
-constexpr uint64_t kWsWaitNs = 2000000000ull;  // 2 s bound per pipeline wait
 constexpr uint32_t kWsAccCols = 128;
 
 #include "ws_units.inc"
@@ -126,6 +125,7 @@ struct WsShared {
   int* next_row;   // [4]: row, first rating, last rating
   int* abort;
   uint32_t* taddr;
+  uint64_t wait_ns;  // bound of every pipeline wait (SweepArgs::wait_ns)
 };
 
 __host__ __device__ inline int ws_fixed_bytes(int nb) {
@@ -162,6 +162,7 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   w.next_row = q;
   w.abort = q + 4;
   w.taddr = reinterpret_cast<uint32_t*>(q + 5);
+  w.wait_ns = 0;
   return w;
 }
 
@@ -173,16 +174,17 @@ __device__ __forceinline__ uint64_t ws_gtimer() {
 
 // Bounded wait by one thread: polls without a suspend hint (a suspended
 // thread resumes late, and every hand-off of the pipeline pays for it), and
-// gives up (setting abort) after kWsWaitNs of wall-clock time, or as soon as
-// another role has aborted.
-__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// gives up (setting abort) after `limit` ns of wall-clock time (2 s unless
+// the caller set another bound), or as soon as another role has aborted.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                        uint64_t limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = ws_gtimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 31u) == 0u) {
       if (*abort) return false;
-      if (ws_gtimer() - t0 > kWsWaitNs) break;
+      if (ws_gtimer() - t0 > limit) break;
     }
   }
   *abort = 1;
@@ -192,8 +194,9 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile
 // The same by a whole warp: every lane waits (and so acquires what the
 // barrier publishes); the outcome is made uniform across the warp, so no
 // lane leaves a loop that its neighbours stay in.
-__device__ __forceinline__ bool ws_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  const bool ok = ws_wait(bar, parity, abort);
+__device__ __forceinline__ bool ws_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                             uint64_t limit) {
+  const bool ok = ws_wait(bar, parity, abort, limit);
   return __all_sync(0xffffffffu, ok) != 0;
 }
 
@@ -308,14 +311,14 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   for (;;) {
     if (t == 0) {
       // the slot is free once every gather thread has read the previous row
-      const bool ok = q == 0 || ws_wait(w.row_read, (uint32_t)(q - 1) & 1u, w.abort);
+      const bool ok = q == 0 || ws_wait(w.row_read, (uint32_t)(q - 1) & 1u, w.abort, w.wait_ns);
       w.next_row[0] = ok ? wk.x : -1;
       w.next_row[1] = wk.y;
       w.next_row[2] = wk.z;
       mbar_arrive(w.row_ready);
       if (ok && wk.x >= 0) next_slot = atomicAdd(counter, 1);
     }
-    if (!ws_wait_warp(w.row_ready, (uint32_t)q & 1u, w.abort)) break;
+    if (!ws_wait_warp(w.row_ready, (uint32_t)q & 1u, w.abort, w.wait_ns)) break;
     const int row = w.next_row[0];
     const int e0 = w.next_row[1], e1 = row >= 0 ? w.next_row[2] : e0;
     mbar_arrive(w.row_read);
@@ -356,7 +359,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
           rn[u] = __ldg(a.val + e + 4 * NB + k);
         }
       }
-      if (!ws_wait_warp(&w.empty[s], ((nn / (uint32_t)S) & 1u) ^ 1u, w.abort)) {
+      if (!ws_wait_warp(&w.empty[s], ((nn / (uint32_t)S) & 1u) ^ 1u, w.abort, w.wait_ns)) {
         stop = true;
         break;
       }
@@ -417,13 +420,13 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
   int q = 0;
   for (;;) {
     const int s = ws_slot(n, S);
-    if (!ws_wait(&w.full[s], (n / (uint32_t)S) & 1u, w.abort)) break;
+    if (!ws_wait(&w.full[s], (n / (uint32_t)S) & 1u, w.abort, w.wait_ns)) break;
     tc_fence_after();
     const StageMeta m = w.meta[s];
     const RowRec r = w.recs[m.rec];
     const int b = q & 1;
     if (m.flags & 1) {
-      if (!ws_wait(&w.acc_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, w.abort)) break;
+      if (!ws_wait(&w.acc_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, w.abort, w.wait_ns)) break;
       tc_fence_after();
     }
     const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
@@ -503,7 +506,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
   int q = 0;
   for (;;) {
     const int b = q & 1;
-    if (!ws_wait_warp(&w.acc_full[b], (uint32_t)(q >> 1) & 1u, w.abort)) return;
+    if (!ws_wait_warp(&w.acc_full[b], (uint32_t)(q >> 1) & 1u, w.abort, w.wait_ns)) return;
     tc_fence_after();
     const RowRec r = w.recs[q % kWsRecs];
     if (r.row < 0) {
@@ -511,14 +514,14 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
       for (int i = 0; i < C; ++i) {
         const int c = (q + i) % C;
         const int use = (q + i) / C;
-        if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)use & 1u) ^ 1u, w.abort)) return;
+        if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)use & 1u) ^ 1u, w.abort, w.wait_ns)) return;
         if (m == 0) reinterpret_cast<int*>(w.slots + c * slotf)[0] = -1;
         mbar_arrive(&w.slot_full[c]);
       }
       return;
     }
     const int c = q % C;
-    if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)(q / C) & 1u) ^ 1u, w.abort)) return;
+    if (!ws_wait_warp(&w.slot_empty[c], ((uint32_t)(q / C) & 1u) ^ 1u, w.abort, w.wait_ns)) return;
     float* slot = w.slots + c * slotf;
     float* tiles = slot + 4;
     float* diag0 = tiles + G.ntile * kWsTileF;
@@ -570,11 +573,11 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
 __device__ __forceinline__ int tidx(int I, int J) { return I * (I + 1) / 2 + J; }
 
 // Blocked right-looking Cholesky of the slot's tiles by one warp.  Returns
-// false if a pivot (of rows 0..K-1) fell below kPivotRel of its starting
-// diagonal; row K (the bordered right-hand side) and the padding rows are
-// never tested.
+// false if a pivot (of rows 0..K-1) failed the pivot rule of tile_chol.cuh
+// (at or below prel times its starting diagonal); row K (the bordered
+// right-hand side) and the padding rows are never tested.
 __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const float* diag0, float* rinv,
-                                            const uint16_t* sched, int lane) {
+                                            const uint16_t* sched, int lane, float prel) {
   bool fail = false;
   const uint16_t* sched_round = sched + 32 * G.nround;
   for (int p = 0; p < G.g; ++p) {
@@ -594,9 +597,9 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
       {  // without branches: the lanes stay converged through the chain
         const float d0 = d0v[c];
         const bool real = idx < G.K;  // row K (never a pivot) and padding rows are not tested
-        const bool bad = real && !(piv > kPivotRel * d0);
+        const bool bad = real && (!(piv > prel * d0) || !(piv > 0.f));
         fail = fail || bad;
-        const float fix = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+        const float fix = pivot_stand_in(piv, d0);
         piv = bad ? fix : (real ? piv : fmaxf(piv, FLT_MIN));
       }
       const float rd = rsqrtf(piv);
@@ -694,7 +697,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
   const uint32_t tw = *a.tp;
   const int K = G.K;
   for (int qc = 0;; ++qc) {
-    if (!ws_wait_warp(&w.slot_full[c], (uint32_t)qc & 1u, w.abort)) return;
+    if (!ws_wait_warp(&w.slot_full[c], (uint32_t)qc & 1u, w.abort, w.wait_ns)) return;
     const int row = reinterpret_cast<const int*>(slot)[0];
     if (row < 0) return;
     for (int qd = lane; 4 * qd < K; qd += 32) {
@@ -704,7 +707,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
       if (4 * qd + 2 < K) zv[4 * qd + 2] = z.z;
       if (4 * qd + 3 < K) zv[4 * qd + 3] = z.w;
     }
-    const bool ok = ws_cholesky(G, T, diag0, rinv, w.sched, lane);
+    const bool ok = ws_cholesky(G, T, diag0, rinv, w.sched, lane, a.pivot_rel);
     if (ok) {
       // w = y + z with y = row K of L; u = L^-T w by 8-row blocks from the
       // bottom: every lane solves the block's 8 x 8 system against the
@@ -773,7 +776,8 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
                                                  int* status) {
   extern __shared__ __align__(1024) uint8_t smem_ws[];
   const WsGeom G(a.K);
-  const WsShared w = ws_carve(smem_ws, G, S, C, NB);
+  WsShared w = ws_carve(smem_ws, G, S, C, NB);
+  w.wait_ns = a.wait_ns;
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {

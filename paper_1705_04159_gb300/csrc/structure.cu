@@ -166,6 +166,12 @@ __global__ void check_indices(const int32_t* __restrict__ row, const int32_t* __
   }
 }
 
+__global__ void check_finite(const float* __restrict__ v, int64_t n, int* status) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[e])) atomicOr(status, kStatusValue);
+}
+
 // Fixed-shape FP64 sum: block b sums elements b, b + G*256, ... in a fixed
 // pattern, then one thread adds the block sums in block order.
 constexpr int kMeanBlocks = 512;
@@ -341,12 +347,15 @@ int build_structure(Handle* h, const int32_t* d_row, const int32_t* d_col, const
   const int64_t nnz = h->nnz;
   if (nnz > 0) {
     check_indices<<<grid_for(nnz, 256), 256, 0, st>>>(d_row, d_col, nnz, h->M, h->N, h->status);
+    check_finite<<<grid_for(nnz, 256), 256, 0, st>>>(d_val, nnz, h->status);
     BPMF_CUDA_CHECK(cudaGetLastError());
     int st_h = 0;
     BPMF_CUDA_CHECK(cudaMemcpyAsync(&st_h, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
-    if (st_h & kStatusIndex) {
-      set_error("bpmf_init: a rating index is outside [0, M) x [0, N)");
+    if (st_h & (kStatusIndex | kStatusValue)) {
+      BPMF_CUDA_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+      set_error(st_h & kStatusIndex ? "bpmf_init: a rating index is outside [0, M) x [0, N)"
+                                    : "bpmf_init: a rating is not finite");
       return BPMF_EINVAL;
     }
   }
@@ -419,12 +428,15 @@ int sort_test_set(Handle* h, const int32_t* d_row, const int32_t* d_col, const f
                   int64_t n, uint32_t* keys, uint32_t* keys_sorted, int32_t* ids, int32_t* src) {
   cudaStream_t st = h->stream;
   BPMF_TRY(validate_pairs(h, d_row, d_col, n));
+  check_finite<<<grid_for(n, 256), 256, 0, st>>>(d_val, n, h->status);
+  BPMF_CUDA_CHECK(cudaGetLastError());
   int st_h = 0;
   BPMF_CUDA_CHECK(cudaMemcpyAsync(&st_h, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   BPMF_CUDA_CHECK(cudaStreamSynchronize(st));
-  if (st_h & kStatusIndex) {
+  if (st_h & (kStatusIndex | kStatusValue)) {
     BPMF_CUDA_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-    set_error("bpmf_set_test: a test index is outside [0, M) x [0, N)");
+    set_error(st_h & kStatusIndex ? "bpmf_set_test: a test index is outside [0, M) x [0, N)"
+                                  : "bpmf_set_test: a test rating is not finite");
     return BPMF_EINVAL;
   }
   gather_keys<<<grid_for(n, 256), 256, 0, st>>>(d_row, keys, n);

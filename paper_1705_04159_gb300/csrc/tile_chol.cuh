@@ -19,9 +19,16 @@
 
 namespace gb {
 
-// A pivot below this fraction of its column's starting diagonal means the
-// FP32 factorisation lost too many digits there: the row is redone in FP64.
-constexpr float kPivotRel = 1e-4f;
+// Pivot rule: a pivot at or below prel (SweepArgs::pivot_rel) times its
+// column's starting diagonal means the FP32 factorisation may have lost too
+// many digits there, and the row is redone in FP64.  The pivot ratio of
+// column k is 1 / (A_kk (A_k^-1)_kk) for the leading block A_k, so a small
+// ratio marks an ill-conditioned row; a non-positive pivot always fails.
+// A failed pivot is replaced by this finite stand-in so that the rest of the
+// factorisation stays finite (its output is discarded).
+__device__ __forceinline__ float pivot_stand_in(float piv, float d0) {
+  return fmaxf(fabsf(piv), fabsf(d0) * 1e-4f) + FLT_MIN;
+}
 
 // Tile edge used for latent dimension K.
 __host__ __device__ constexpr int tile_edge_for(int K) {
@@ -200,11 +207,11 @@ __device__ __forceinline__ CholSmem carve_chol(float* Lr, float* tail, const Til
 // A panel is partial only when it also holds column K, and then it is the
 // last tile column, so trailing updates always see full panels.
 // Preconditions: acc formed by form_bordered, zv holds the normals, the block
-// is synchronised.  Returns false (on all threads) if a pivot failed; xout is
-// then not written.
+// is synchronised.  Returns false (on all threads) if a pivot failed the rule
+// above (prel); xout is then not written.
 template <int TM>
 __device__ bool chol_solve_write(float (&acc)[TM][TM], bool active, int ty, int tx,
-                                 const TileGeom& G, const CholSmem& cs, int* fail_sh,
+                                 const TileGeom& G, const CholSmem& cs, float prel, int* fail_sh,
                                  float* __restrict__ xout) {
   const int K = G.K, KA = G.KA, LDS = G.LDS;
   const int gc = (K + TM - 1) / TM;
@@ -218,9 +225,9 @@ __device__ bool chol_solve_write(float (&acc)[TM][TM], bool active, int ty, int 
         if (j < nc) {
           float piv = acc[j][j];
           const float d0 = cs.diag0[c0 + j];
-          if (!(piv > kPivotRel * d0)) {
+          if (!(piv > prel * d0) || !(piv > 0.f)) {
             *fail_sh = 1;
-            piv = fmaxf(fabsf(piv), fabsf(d0) * kPivotRel) + FLT_MIN;
+            piv = pivot_stand_in(piv, d0);
           }
           const float rd = rsqrtf(piv);
           const float d = piv * rd;

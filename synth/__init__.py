@@ -28,6 +28,13 @@ Recipes (paper Sec. V-B names the public datasets; only their shapes are used):
   (largest expected column degree 230k, largest expected row degree 8,885),
   value = clip(round(3.6 + u.v + N(0, 1)), 1, 5), planted rank 100.
 * ``powerlaw``: the same Chung-Lu construction at any size (parity cases).
+* ``ill_conditioned``: a small case with a state whose row precisions are
+  ill-conditioned for half of the users: those users rate only movies whose
+  factors lie close to a low-dimensional subspace, and the users' prior
+  precision is small, so FP32 cannot factor their rows accurately while FP64
+  can; the other users rate generic movies and stay well conditioned.
+  Ratings are from {-2, -1, 1, 2} with an exact zero sum, so their mean is 0
+  and centring is exact in any precision.
 * ``serving_stream`` / ``serving_job``: a stream of independent jobs with
   Poisson arrivals (rate 20/s) and log-uniform shapes (rows 1k-200k, columns
   1k-50k, ratings 10k-5M, K in {16, 32, 64}), uniformly placed cells.
@@ -43,7 +50,8 @@ import os
 import numpy as np
 
 __all__ = ["Dataset", "tiny", "tiny_dense", "movielens", "chembl", "netflix",
-           "powerlaw", "uniform", "make", "RECIPES", "serving_stream", "serving_job"]
+           "powerlaw", "uniform", "make", "RECIPES", "serving_stream", "serving_job",
+           "ill_conditioned"]
 
 
 @dataclasses.dataclass
@@ -291,6 +299,47 @@ def netflix(seed: int = 0, device: str = "cpu") -> Dataset:
     parts = _split(rng, r, c, val)
     return Dataset("netflix", M, N, K, 2.0, *parts, clip=(1.0, 5.0),
                    note=f"Netflix shape: row exponent {row_expo:.3f}, column exponent {col_expo:.3f}")
+
+
+def ill_conditioned(K: int, n_users: int = 64, seed: int = 0, eps: float = 1e-4,
+                    prior_prec: float = 1e-3, rank: int | None = None):
+    """A small case whose first half of users have ill-conditioned rows.
+
+    Returns (ds, U, V, hyper, bad) with hyper laid out as the sampler's state
+    [Lambda_U, mu_U, Lambda_V, mu_V] and bad the ids of the ill-conditioned
+    users.  Movies 0 .. N/2 - 1 have factors B c_j + eps n_j (B of rank
+    `rank`, default K // 4, entries of std 0.3); the rest are generic
+    N(0, 0.3^2).  User i < n_users / 2 rates 2K of the first kind, the others
+    4K of the second.  Lambda_U = prior_prec I, mu_U = 0; Lambda_V = I."""
+    rng = np.random.default_rng(seed)
+    r = rank or max(1, K // 4)
+    N = 16 * K
+    half = N // 2
+    B = rng.normal(0.0, 1.0, size=(r, K)) / math.sqrt(r)
+    V = np.empty((N, K))
+    V[:half] = 0.3 * (rng.normal(size=(half, r)) @ B + eps * rng.normal(size=(half, K)))
+    V[half:] = 0.3 * rng.normal(size=(N - half, K))
+    rows, cols = [], []
+    nb = n_users // 2
+    for i in range(n_users):
+        d, lo = (2 * K, 0) if i < nb else (4 * K, half)
+        rows.append(np.full(d, i))
+        cols.append(lo + rng.choice(half, size=d, replace=False))
+    rows = np.concatenate(rows).astype(np.int32)
+    cols = np.concatenate(cols).astype(np.int32)
+    n = len(rows)
+    mag = rng.integers(1, 3, size=n // 2).astype(np.float32)
+    vals = np.concatenate([mag, -mag])
+    if n % 2:
+        vals = np.concatenate([vals, np.zeros(1, np.float32)])
+    vals = vals[rng.permutation(n)].astype(np.float32)
+    empty_i = np.zeros(0, np.int32)
+    ds = Dataset(f"ill_conditioned_K{K}", n_users, N, K, 2.0, rows, cols, vals, empty_i, empty_i,
+                 np.zeros(0, np.float32), note="ill-conditioned half of the users")
+    U = 0.3 * rng.normal(size=(n_users, K))
+    hyper = np.concatenate([(prior_prec * np.eye(K)).ravel(), np.zeros(K), np.eye(K).ravel(),
+                            np.zeros(K)])
+    return ds, U.astype(np.float32), V.astype(np.float32), hyper, np.arange(nb)
 
 
 def serving_stream(n_jobs: int = 256, rate: float = 20.0, seed: int = 0) -> list:

@@ -129,6 +129,7 @@ def test_struct_mirrors_match_the_c_layout(tmp_path, pyname, ctype):
     ("bpmf_set_graph", (1,)), ("bpmf_test_rmse", (None, None)),
     ("bpmf_get_state", (None, None, None, None, 0)), ("bpmf_get_thresholds", (0, None)),
     ("bpmf_get_sweep_info", (0, None, None)), ("bpmf_set_timing", (1,)),
+    ("bpmf_set_limits", (64, 0)),
 ])
 def test_null_handle_is_rejected_with_a_message(libpath, name, args):
     """Every entry point that takes a handle checks it before anything else
@@ -158,3 +159,29 @@ def test_missing_library_fails_loudly():
                        cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == "raised"
+
+
+@pytest.mark.parametrize("field,value", [
+    ("alpha", 0.0), ("alpha", -1.0), ("alpha", float("nan")), ("alpha", float("inf")),
+    ("beta0", float("inf")), ("beta0", 0.0), ("nu0", float("nan")), ("nu0", float("inf")),
+    ("pivot_rel", 1.0), ("pivot_rel", -0.1), ("pivot_rel", float("nan")),
+])
+def test_init_rejects_non_positive_or_non_finite_settings(libpath, field, value):
+    """The row precision Lambda_s + alpha sum v v^T is positive definite for
+    any alpha > 0, so the FP64 redo can only fail by rounding once alpha is
+    positive and finite; the configuration is refused before the device is
+    touched otherwise."""
+    import numpy as np
+    import paper_1705_04159_gb300 as bp
+    cfg = bp.bpmf_config_default(4)
+    setattr(cfg, field, value)
+    with pytest.raises(bp.BpmfError) as e:
+        bp.bpmf_init(4, 4, np.zeros(1, np.int32), np.zeros(1, np.int32), np.ones(1, np.float32),
+                     cfg, stream=0)
+    assert e.value.code == bp.EINVAL
+
+
+def test_limits_reject_a_gamma_cap_above_the_default(libpath):
+    import paper_1705_04159_gb300 as bp
+    L = bp.lib()
+    assert L.bpmf_set_limits(None, 65, 0) == bp.EINVAL

@@ -32,3 +32,5 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the steps reported are the steps timed: their total fits in the run
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= d["wall_s"] * 1.01

@@ -77,6 +77,13 @@ def test_hyper_parity(gpu_lib, name):
             gL = s.hyper()[2 * side]
             gm = s.hyper()[2 * side + 1]
             assert np.linalg.norm(gL - Lam) <= 1e-4 * np.linalg.norm(Lam)
+            # element by element, each entry against its diagonal scale
+            # sqrt(Lam_ii Lam_jj) (the largest an entry of an SPD matrix can be)
+            scale = np.sqrt(np.outer(np.diag(Lam), np.diag(Lam)))
+            assert np.max(np.abs(gL - Lam) / scale) <= 1e-4
+            # and the scatter the same way
+            sscale = np.sqrt(np.outer(np.diag(oS), np.diag(oS)))
+            assert np.max(np.abs(S - oS) / sscale) <= 1e-5
             assert np.max(np.abs(gm - mu)) <= 1e-4 * (np.abs(mu).max() + 1.0 / np.sqrt(
                 np.diag(Lam).min()))
 

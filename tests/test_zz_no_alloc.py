@@ -1,17 +1,21 @@
-"""The allocation-free entry point bpmf_hyper_stats_noalloc against the
-library's own hyperparameter statistics.
+"""The allocation-free entry point bpmf_hyper_stats_noalloc against the FP64
+oracle and against the library's own hyperparameter statistics.
 
 Callers that cannot allocate device memory at call time (a fixed pool or an
 arena they do not own, or a host that forbids cudaMalloc after start-up) use
 bpmf_hyper_stats_noalloc, whose scratch is a fixed array compiled into the
 library.  Its row mean and centred scatter must equal, within the tolerance of
-the other statistics tests, what bpmf_sample_hyper computes for the same
-factors (read back with bpmf_get_hyper_stats), on two calls in a row that
-reuse the shared scratch.  This file is collected last on purpose.
+the other statistics tests, the oracle's statistics of the same factors and
+what bpmf_sample_hyper computes for them (read back with
+bpmf_get_hyper_stats), on two calls in a row that reuse the shared scratch,
+and on a matrix as tall as the Netflix-shaped users side at the largest K,
+where the fixed scratch leaves the fewest blocks (so each block sums the most
+rows).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -43,6 +47,32 @@ def test_noalloc_stats_match_existing_entry_point_twice(gpu_lib):
         got_S = S.cpu().numpy().reshape(K, K)
         assert np.max(np.abs(got_xbar - ref_xbar)) <= 1e-6 * (np.abs(ref_xbar).max() + U.std())
         assert np.linalg.norm(got_S - ref_S) <= 1e-5 * np.linalg.norm(ref_S)
+        oxbar, oS = oracle.hyper_stats(U.astype(np.float64))
+        assert np.max(np.abs(got_xbar - oxbar)) <= 1e-6 * (np.abs(oxbar).max() + U.std())
+        assert np.linalg.norm(got_S - oS) <= 1e-5 * np.linalg.norm(oS)
+
+
+def test_noalloc_stats_tall_matrix_at_the_largest_k(gpu_lib):
+    """480,189 rows at K = 128: the 2 MiB scratch holds 15 block partials, so
+    each block reduces about 32k rows; the FP32 sums are moved to FP64 every
+    1024 rows, which keeps the result within the statistics tolerance."""
+    import torch
+    bp = gpu_lib
+    R, K = 480189, 128
+    rng = np.random.default_rng(33)
+    U = (0.3 * rng.normal(size=(R, K)) + 0.05).astype(np.float32)
+    X = torch.from_numpy(U).cuda()
+    xbar = torch.full((K,), float("nan"), dtype=torch.float64, device="cuda")
+    S = torch.full((K * K,), float("nan"), dtype=torch.float64, device="cuda")
+    bp.bpmf_hyper_stats_noalloc(X, R, K, xbar, S)
+    torch.cuda.synchronize()
+    oxbar, oS = oracle.hyper_stats(U.astype(np.float64))
+    got_S = S.cpu().numpy().reshape(K, K)
+    assert np.max(np.abs(xbar.cpu().numpy() - oxbar)) <= 1e-6 * (np.abs(oxbar).max() + U.std())
+    assert np.linalg.norm(got_S - oS) <= 1e-5 * np.linalg.norm(oS)
+    # element by element, against the diagonal scale of each entry
+    scale = np.sqrt(np.outer(np.diag(oS), np.diag(oS)))
+    assert np.max(np.abs(got_S - oS) / scale) <= 1e-5
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(gpu_lib):
