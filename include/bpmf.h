@@ -106,13 +106,13 @@ typedef struct {
                          starting diagonal (Lambda*_kk) is redrawn from scratch in FP64.
                          The pivot ratio of column k is 1 / (Lambda*_kk (A_k^-1)_kk) for the
                          leading block A_k, a lower bound on how far the row's conditioning
-                         lets FP32 drift; 0 flags only pivots <= 0.  Default 3e-2 */
+                         lets FP32 drift; 0 flags only pivots <= 0.  Default 5e-2 */
 } bpmf_config;
 
 /* Fills `cfg` with the defaults: path MIXED, alpha 2, beta0 2, nu0 K,
  * mu0 = 0, W0 = I, seed 0, order 0, burnin 0, automatic thresholds,
  * autotune 0 (fixed defaults: the kernel choice, hence the FP32 rounding of
- * every draw, does not depend on timings), pivot_rel 3e-2. */
+ * every draw, does not depend on timings), pivot_rel 5e-2. */
 BPMF_API void bpmf_config_default(bpmf_config *cfg, int32_t K);
 
 /* Creates a sampler for the M x N training ratings given as nnz triples
@@ -381,6 +381,17 @@ BPMF_API int bpmf_server_stats(bpmf_server_t *s, int64_t stats[6]);
 
 /* Seconds since the server started (the clock of bpmf_job_result). */
 BPMF_API double bpmf_server_clock(bpmf_server_t *s);
+
+/* Device trace of finished job `id` (measurement; the paper has no
+ * counterpart): for each of its first iterations (up to 256), the device
+ * times in ms at which the iteration's launches began (start_ms[i]) and
+ * ended (end_ms[i]), from CUDA events on the job's stream measured against
+ * one reference event recorded when the server was created, so the
+ * intervals of all jobs of a server share one clock.  Writes min(n, *n_out)
+ * entries of the host arrays; *n_out = the iterations traced.
+ * Errors: EINVAL (unknown job, bad arguments), EBUSY (not done yet). */
+BPMF_API int bpmf_server_trace(bpmf_server_t *s, int64_t id, int32_t n, double *start_ms,
+                               double *end_ms, int32_t *n_out);
 
 /* Finishes every submitted job, stops the worker and frees the server. */
 BPMF_API void bpmf_server_destroy(bpmf_server_t *s);

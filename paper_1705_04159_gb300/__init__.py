@@ -136,6 +136,7 @@ def lib():
         L.bpmf_server_stats.argtypes = [P, P]
         L.bpmf_server_clock.argtypes = [P]
         L.bpmf_server_clock.restype = C.c_double
+        L.bpmf_server_trace.argtypes = [P, i64, i32, P, P, P]
         L.bpmf_server_destroy.argtypes = [P]
         L.bpmf_server_destroy.restype = None
         L.bpmf_strerror.argtypes = [C.c_int]
@@ -430,6 +431,18 @@ def bpmf_server_clock(srv):
     return lib().bpmf_server_clock(srv)
 
 
+def bpmf_server_trace(srv, jid, n=256):
+    """(start_ms, end_ms) arrays of the device interval of each traced
+    iteration of finished job `jid`, on the server's shared clock."""
+    a = np.empty(n)
+    b = np.empty(n)
+    m = C.c_int32()
+    _check(lib().bpmf_server_trace(srv, int(jid), int(n), a.ctypes.data, b.ctypes.data,
+                                   C.byref(m)), "bpmf_server_trace")
+    k = min(n, m.value)
+    return a[:k], b[:k]
+
+
 def bpmf_server_destroy(srv):
     if srv:
         lib().bpmf_server_destroy(srv)
@@ -594,6 +607,9 @@ class Server:
 
     def stats(self):
         return bpmf_server_stats(self.h)
+
+    def trace(self, jid, n=256):
+        return bpmf_server_trace(self.h, jid, n)
 
     def clock(self):
         return bpmf_server_clock(self.h)

@@ -259,7 +259,7 @@ void bpmf_config_default(bpmf_config* c, int32_t K) {
   c->tiny_max = -1;
   c->heavy_kernel = 0;
   c->autotune = 0;
-  c->pivot_rel = 3e-2;
+  c->pivot_rel = 5e-2;
 }
 
 const char* bpmf_strerror(int code) {

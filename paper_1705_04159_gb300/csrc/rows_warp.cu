@@ -76,18 +76,23 @@ __device__ __forceinline__ void warp_stage(const SweepArgs& a, float* T, int64_t
     j = __ldg(a.idx + e0 + lane);
     r = __ldg(a.val + e0 + lane);
   }
+  // every lane runs the same number of passes, so that the shuffles (full
+  // mask) are reached by all 32 lanes; lanes past the end copy nothing
   if ((K & 3) == 0) {
-    const int Q = K >> 2;
-    for (int e = lane; e < cnt * Q; e += 32) {
-      const int c = e / Q, q = e - c * Q;
+    const int Q = K >> 2, n = cnt * Q;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+      const int e = e0 + lane;
+      const int c = e < n ? e / Q : 0, q = e < n ? e - c * Q : 0;
       const int32_t jc = __shfl_sync(0xffffffffu, j, c);
-      cp_async16(T + c * W::LDT + 4 * q, a.Vo + (int64_t)jc * K + 4 * q);
+      if (e < n) cp_async16(T + c * W::LDT + 4 * q, a.Vo + (int64_t)jc * K + 4 * q);
     }
   } else {
-    for (int e = lane; e < cnt * K; e += 32) {
-      const int c = e / K, k = e - c * K;
+    const int n = cnt * K;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+      const int e = e0 + lane;
+      const int c = e < n ? e / K : 0, k = e < n ? e - c * K : 0;
       const int32_t jc = __shfl_sync(0xffffffffu, j, c);
-      cp_async4(T + c * W::LDT + k, a.Vo + (int64_t)jc * K + k);
+      if (e < n) cp_async4(T + c * W::LDT + k, a.Vo + (int64_t)jc * K + k);
     }
   }
   cp_async_commit();

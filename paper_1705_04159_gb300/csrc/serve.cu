@@ -14,7 +14,10 @@
 // and the next queued job is admitted while the others keep running.  Each
 // job's draws depend only on its own data, configuration and seed (counter
 // based Philox, fixed reduction orders), so a job's result is bitwise the
-// same alone and in any mix.
+// same alone and in any mix.  The device interval of each of a job's first
+// iterations is recorded with CUDA events against one reference event of the
+// server (bpmf_server_trace), which shows whether the iterations of resident
+// jobs ran on the device at the same time.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -35,6 +38,7 @@ namespace gb {
 namespace {
 
 constexpr int kLookahead = 2;  // iterations queued ahead per resident job
+constexpr int kTraceIters = 256;  // iterations per job whose device interval is recorded
 
 struct Job {
   int64_t id = 0;
@@ -52,6 +56,10 @@ struct Job {
   bpmf_t* h = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;  // recorded after the newest queued iteration
+  // device trace: timing events before and after each of the first
+  // kTraceIters iterations, turned into ms against the server's reference
+  std::vector<cudaEvent_t> ev_it;
+  std::vector<double> t_it;
   int32_t launched = 0;
   bool done = false;
   bpmf_job_result res{};
@@ -97,6 +105,7 @@ struct Server {
   int64_t n_done = 0, peak_resident = 0, peak_bytes = 0;
   bool stop = false;
   std::thread worker;
+  cudaEvent_t ref = nullptr;  // time origin of the device traces
 
   void run();
   void admit(const std::shared_ptr<Job>& j);
@@ -112,6 +121,16 @@ void Server::admit(const std::shared_ptr<Job>& jp) {
       cudaEventCreateWithFlags(&j.ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     rc = BPMF_ECUDA;
+  }
+  const int32_t ntr = std::min(j.iterations, kTraceIters);
+  for (int32_t e = 0; rc == BPMF_OK && e < 2 * ntr; ++e) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      cudaGetLastError();
+      rc = BPMF_ECUDA;
+    } else {
+      j.ev_it.push_back(ev);
+    }
   }
   bpmf_config cfg = j.cfg;
   cfg.mu0 = j.mu0.empty() ? nullptr : j.mu0.data();
@@ -140,9 +159,18 @@ void Server::launch_more(Job& j) {
   const int32_t target = std::min(j.iterations, j.launched + kLookahead);
   Handle* h = reinterpret_cast<Handle*>(j.h);
   while (j.launched < target) {
+    const bool traced = 2 * (size_t)j.launched + 1 < j.ev_it.size();
+    if (traced && cudaEventRecord(j.ev_it[2 * j.launched], j.st) != cudaSuccess) {
+      j.res.status = BPMF_ECUDA;
+      break;
+    }
     const int rc = step_async(h);
     if (rc != BPMF_OK) {
       j.res.status = rc;
+      break;
+    }
+    if (traced && cudaEventRecord(j.ev_it[2 * j.launched + 1], j.st) != cudaSuccess) {
+      j.res.status = BPMF_ECUDA;
       break;
     }
     ++j.launched;
@@ -174,6 +202,18 @@ void Server::finish(Job& j) {
     bpmf_destroy(j.h);
     j.h = nullptr;
   }
+  // the stream has been synchronised: every recorded event has completed
+  const int32_t ntr = std::min<int32_t>(j.launched, (int32_t)(j.ev_it.size() / 2));
+  for (int32_t e = 0; e < 2 * ntr; ++e) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ref, j.ev_it[e]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = NAN;
+    }
+    j.t_it.push_back((double)ms);
+  }
+  for (cudaEvent_t e : j.ev_it) cudaEventDestroy(e);
+  j.ev_it.clear();
   if (j.ev) cudaEventDestroy(j.ev);
   if (j.st) cudaStreamDestroy(j.st);
   j.ev = nullptr;
@@ -281,6 +321,14 @@ int bpmf_server_create(bpmf_server_t** out, int64_t budget_bytes, int32_t max_re
       return BPMF_ECUDA;
     }
     budget_bytes = (int64_t)(0.8 * (double)fr);
+  }
+  if (cudaEventCreate(&s->ref) != cudaSuccess || cudaEventRecord(s->ref, 0) != cudaSuccess ||
+      cudaEventSynchronize(s->ref) != cudaSuccess) {
+    cudaGetLastError();
+    if (s->ref) cudaEventDestroy(s->ref);
+    delete s;
+    set_error("bpmf_server_create: reference event failed");
+    return BPMF_ECUDA;
   }
   s->budget = budget_bytes;
   s->max_resident = max_resident > 0 ? max_resident : 16;
@@ -392,7 +440,33 @@ void bpmf_server_destroy(bpmf_server_t* ss) {
   }
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->ref) cudaEventDestroy(s->ref);
   delete s;
+}
+
+int bpmf_server_trace(bpmf_server_t* ss, int64_t id, int32_t n, double* start_ms, double* end_ms,
+                      int32_t* n_out) {
+  Server* s = reinterpret_cast<Server*>(ss);
+  if (!s || n < 0 || (n > 0 && (!start_ms || !end_ms)) || !n_out) {
+    set_error("bpmf_server_trace: invalid argument");
+    return BPMF_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) {
+    set_error("bpmf_server_trace: unknown job");
+    return BPMF_EINVAL;
+  }
+  const Job& j = *it->second;
+  if (!j.done) return BPMF_EBUSY;
+  const int32_t have = (int32_t)(j.t_it.size() / 2);
+  const int32_t m = std::min(n, have);
+  for (int32_t i = 0; i < m; ++i) {
+    start_ms[i] = j.t_it[2 * i];
+    end_ms[i] = j.t_it[2 * i + 1];
+  }
+  *n_out = have;
+  return BPMF_OK;
 }
 
 }  // extern "C"

@@ -115,3 +115,51 @@ def test_submit_rejects_bad_jobs(gpu_lib):
         assert r.status == bp.EINVAL
         r, _ = srv.result(srv.submit(10, 10, [0, 1], [0, 1], [1.0, 2.0], 8, 2))
         assert r.status == 0
+
+
+def _overlap(a0, a1, b0, b1):
+    """Total length of the intersection of interval sets a and b."""
+    tot = 0.0
+    for s, e in zip(a0, a1):
+        for t, f in zip(b0, b1):
+            tot += max(0.0, min(e, f) - max(s, t))
+    return tot
+
+
+def test_resident_jobs_run_on_the_device_at_the_same_time(gpu_lib):
+    """Device-side evidence of co-scheduling: the per-iteration device
+    intervals (CUDA events on each job's stream, one shared reference) of
+    two small jobs submitted together overlap for most of their length, while
+    each iteration takes about as long as it does alone.  Had the device run
+    one job's kernels at a time, overlapping iterations would each stretch to
+    about twice their time alone.  Results stay bitwise the same."""
+    bp = gpu_lib
+    ds = synth.uniform(600, 400, 6000, 16, seed=61)
+    iters = 40
+
+    def submit(srv, seed):
+        return srv.submit(ds.M, ds.N, ds.train_row, ds.train_col, ds.train_val, 16, iters,
+                          alpha=ds.alpha, seed=seed, path=bp.PATH_BINNED, want_factors=True)
+
+    alone = []
+    with bp.Server(max_resident=1) as srv:
+        for seed in (1, 2):
+            jid = submit(srv, seed)
+            r, (U, V) = srv.result(jid)
+            assert r.status == 0
+            t0, t1 = srv.trace(jid)
+            assert len(t0) == iters and np.all(t1 >= t0)
+            alone.append((U, V, np.median(t1 - t0)))
+    with bp.Server(max_resident=2) as srv:
+        ids = [submit(srv, seed) for seed in (1, 2)]
+        res = [srv.result(j) for j in ids]
+        tr = [srv.trace(j) for j in ids]
+    for (r, (U, V)), (Ua, Va, _) in zip(res, alone):
+        assert r.status == 0 and np.array_equal(U, Ua) and np.array_equal(V, Va)
+    (a0, a1), (b0, b1) = tr
+    # most of each job's device time overlaps the other job's iterations
+    ov = _overlap(a0, a1, b0, b1)
+    assert ov > 0.5 * min(np.sum(a1 - a0), np.sum(b1 - b0)), (ov, np.sum(a1 - a0), np.sum(b1 - b0))
+    # and an overlapped iteration is not stretched to twice its time alone
+    for (s, e), (_, _, d_alone) in zip(tr, alone):
+        assert np.median(e - s) < 1.5 * d_alone, (np.median(e - s), d_alone)
