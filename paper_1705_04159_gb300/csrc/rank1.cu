@@ -23,6 +23,7 @@
 // tau - t, so their dependence chains (a square root and two divisions per
 // column) overlap instead of running one after another.
 #include <cuda_runtime.h>
+#include <float.h>
 
 #include "bpmf_impl.cuh"
 #include "rows.cuh"
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256, 2)
     const int i = lane + 32 * m;
     const float lii = i < K ? L[tri(i) + i] : 1.f;
     rd[m] = i < K ? 1.0f / lii : 0.f;
-    if (i < K && !(lii * lii > a.pivot_rel * d0[m])) bad = true;
+    if (i < K && !(lii * lii > fmaxf(a.pivot_rel * d0[m], FLT_MIN))) bad = true;
   }
   if (__any_sync(0xffffffffu, bad)) {
     if (lane == 0) a.flag_rows[atomicAdd(a.flag_count, 1)] = row;

@@ -321,7 +321,7 @@ __device__ __forceinline__ bool tc_cholesky(const TileGeom& G, const TcSmem& s, 
         const bool live = j < nc;
         float piv = __shfl_sync(0xffffffffu, v[j], b0 + j);
         const float d0 = s.diag0[c0 + (live ? j : 0)];
-        if (live && (!(piv > prel * d0) || !(piv > 0.f))) {
+        if (live && !(piv > pivot_threshold(prel, d0))) {
           if (lane == b0 + j) s.flags[0] = 1;
           piv = pivot_stand_in(piv, d0);
         }

@@ -63,6 +63,21 @@ constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (se
 constexpr int kWsTileF = 68;         // floats per 8 x 8 tile (see trow)
 constexpr int kWsGather = 128, kWsDrain = 128;
 constexpr int kWsMmaWarp = 8, kWsConsWarp0 = 9;
+// Warps are issued by the scheduler partition warp % 4.  Partition 0 holds
+// a gather warp, a drain warp and the MMA warp; with six consumers, warp 12
+// (partition 0) stays idle, so that the consumers spread evenly over
+// partitions 1 .. 3 (two each) and take the same time per row: they take
+// rows in turn, so an uneven spread leaves the faster ones waiting (with
+// four, the plain order already puts one on each partition).
+__host__ __device__ constexpr bool ws_skip_warp12(int C) { return C == 6; }
+__host__ __device__ constexpr int ws_warps(int C) { return kWsConsWarp0 + C + (ws_skip_warp12(C) ? 1 : 0); }
+// consumer index of warp w (-1: not a consumer)
+__host__ __device__ constexpr int ws_consumer_of(int w, int C) {
+  return w < kWsConsWarp0 ? -1
+         : !ws_skip_warp12(C) ? (w - kWsConsWarp0 < C ? w - kWsConsWarp0 : -1)
+         : w == 12 ? -1
+         : (w < 12 ? w - kWsConsWarp0 : (w - kWsConsWarp0 - 1 < C ? w - kWsConsWarp0 - 1 : -1));
+}
 constexpr uint32_t kWsPolls = 100000;  // suspending polls of <= 20 us: a 2 s bound (final MMA wait)
 constexpr uint32_t kWsAccCols = 128;
 
@@ -128,14 +143,18 @@ struct WsShared {
   uint64_t wait_ns;  // bound of every pipeline wait (SweepArgs::wait_ns)
 };
 
-__host__ __device__ inline int ws_fixed_bytes(int nb) {
-  // barriers (2 S + 4 + 2 C + 3), stage meta, row records, ratings, next_row, abort, taddr
-  return 8 * (2 * kWsMaxStages + 4 + 2 * kWsMaxCons + 3) + 16 * kWsMaxStages + 16 * kWsRecs +
-         4 * kWsMaxStages * nb + 32;
+// mbarriers: full and empty per stage, full and empty per accumulator, full
+// and empty per consumer slot, fin, row_ready, row_read (an even count, so
+// that what follows stays 16-byte aligned)
+__host__ __device__ inline int ws_nbar(int S, int C) { return (2 * S + 4 + 2 * C + 3 + 1) & ~1; }
+__host__ __device__ inline int ws_fixed_bytes(int nb, int S, int C) {
+  // barriers, stage meta, row records, ratings, next_row, abort, taddr
+  return 8 * ws_nbar(S, C) + 16 * S + 16 * kWsRecs + 4 * S * nb + 32;
 }
 // stages, consumer slots, the trailing-update schedule, then the fixed part
 __host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C, int nb) {
-  return S * ws_stage_bytes(nb) + C * G.slot_floats() * 4 + G.sched_bytes() + ws_fixed_bytes(nb);
+  return S * ws_stage_bytes(nb) + C * G.slot_floats() * 4 + G.sched_bytes() +
+         ws_fixed_bytes(nb, S, C);
 }
 
 __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int S, int C, int nb) {
@@ -146,19 +165,19 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   uint8_t* p = reinterpret_cast<uint8_t*>(w.sched) + G.sched_bytes();
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   w.full = b;
-  w.empty = b + kWsMaxStages;
-  w.acc_full = b + 2 * kWsMaxStages;
+  w.empty = b + S;
+  w.acc_full = b + 2 * S;
   w.acc_empty = w.acc_full + 2;
   w.slot_full = w.acc_empty + 2;
-  w.slot_empty = w.slot_full + kWsMaxCons;
-  w.fin = w.slot_empty + kWsMaxCons;
+  w.slot_empty = w.slot_full + C;
+  w.fin = w.slot_empty + C;
   w.row_ready = w.fin + 1;
   w.row_read = w.fin + 2;
-  p = reinterpret_cast<uint8_t*>(w.fin + 3);
+  p = reinterpret_cast<uint8_t*>(b + ws_nbar(S, C));
   w.meta = reinterpret_cast<StageMeta*>(p);
-  w.recs = reinterpret_cast<RowRec*>(p + 16 * kWsMaxStages);
-  w.rating = reinterpret_cast<float*>(p + 16 * kWsMaxStages + 16 * kWsRecs);
-  int* q = reinterpret_cast<int*>(w.rating + kWsMaxStages * nb);
+  w.recs = reinterpret_cast<RowRec*>(p + 16 * S);
+  w.rating = reinterpret_cast<float*>(p + 16 * S + 16 * kWsRecs);
+  int* q = reinterpret_cast<int*>(w.rating + S * nb);
   w.next_row = q;
   w.abort = q + 4;
   w.taddr = reinterpret_cast<uint32_t*>(q + 5);
@@ -588,20 +607,21 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
 #pragma unroll
     for (int i = 0; i < 8; ++i) ld8(D + trow(i), d[i]);
     float rdv[8];
-    float d0v[8];  // starting diagonals of the panel, off the pivot chain
-    ld8(diag0 + 8 * p, d0v);
+    float thr[8];  // pivot thresholds of the panel, from the starting diagonals
+    ld8(diag0 + 8 * p, thr);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) thr[c] = pivot_threshold(prel, thr[c]);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const int idx = 8 * p + c;
-      float piv = d[c][c];
-      {  // without branches: the lanes stay converged through the chain
-        const float d0 = d0v[c];
-        const bool real = idx < G.K;  // row K (never a pivot) and padding rows are not tested
-        const bool bad = real && (!(piv > prel * d0) || !(piv > 0.f));
-        fail = fail || bad;
-        const float fix = pivot_stand_in(piv, d0);
-        piv = bad ? fix : (real ? piv : fmaxf(piv, FLT_MIN));
-      }
+      // Nothing but the square root stands between one pivot and the next:
+      // the pivot rule is checked beside the chain.  A failed real pivot
+      // leaves NaN or inf in the rest of the factorisation, which is
+      // discarded with the row (the FP64 redo draws it).  The pivots of the
+      // bordered row K and of the padding rows (the last panel only) are not
+      // tested: whatever they turn into stays in entries at or past column K
+      // of rows at or past K, which the draw never reads.
+      const float piv = d[c][c];
+      fail = fail || (8 * p + c < G.K && !(piv > thr[c]));  // without branches
       const float rd = rsqrtf(piv);
       rdv[c] = rd;
       d[c][c] = piv * rd;
@@ -687,7 +707,7 @@ __device__ __forceinline__ bool ws_cholesky(const WsGeom& G, float* T, const flo
 }
 
 __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, const WsShared& w, int C) {
-  const int c = (threadIdx.x >> 5) - kWsConsWarp0;
+  const int c = ws_consumer_of(threadIdx.x >> 5, C);
   const int lane = threadIdx.x & 31;
   float* slot = w.slots + c * G.slot_floats();
   float* T = slot + 4;
@@ -822,7 +842,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
     ws_drain(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
     if ((threadIdx.x & 31) == 0) ws_mma<NB>(G, w, S, tmem);
-  } else if (warp - kWsConsWarp0 < C) {
+  } else if (ws_consumer_of(warp, C) >= 0) {
     ws_consume(a, G, w, C);
   }
   tc_fence_before();
@@ -918,7 +938,7 @@ int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* count
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   const int grid = (int)std::min<int64_t>(num_sms, nrows);
-  kern<<<grid, 32 * (kWsConsWarp0 + C), smem, st>>>(a, S, C, counter, status);
+  kern<<<grid, 32 * ws_warps(C), smem, st>>>(a, S, C, counter, status);
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   return BPMF_OK;

@@ -24,6 +24,11 @@ namespace gb {
 // many digits there, and the row is redone in FP64.  The pivot ratio of
 // column k is 1 / (A_kk (A_k^-1)_kk) for the leading block A_k, so a small
 // ratio marks an ill-conditioned row; a non-positive pivot always fails.
+// The threshold is formed from the starting diagonal alone, off the
+// dependence chain of the factorisation: the pivot meets one comparison.
+__device__ __forceinline__ float pivot_threshold(float prel, float d0) {
+  return fmaxf(prel * d0, FLT_MIN);
+}
 // A failed pivot is replaced by this finite stand-in so that the rest of the
 // factorisation stays finite (its output is discarded).
 __device__ __forceinline__ float pivot_stand_in(float piv, float d0) {
@@ -225,7 +230,7 @@ __device__ bool chol_solve_write(float (&acc)[TM][TM], bool active, int ty, int 
         if (j < nc) {
           float piv = acc[j][j];
           const float d0 = cs.diag0[c0 + j];
-          if (!(piv > prel * d0) || !(piv > 0.f)) {
+          if (!(piv > pivot_threshold(prel, d0))) {
             *fail_sh = 1;
             piv = pivot_stand_in(piv, d0);
           }

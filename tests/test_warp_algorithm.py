@@ -5,13 +5,17 @@ rows_warp.cu splits the work of one row over the 32 lanes of a warp:
     KP x KP square (RB = KP / 8, CB = KP / 4), with the rating sum as column K
     when K < KP and as extra per-row sums on the lanes with l % 4 = 0 when
     K = KP;
-  - the Cholesky: lane i holds row i; column k scales by 1 / sqrt(pivot of
-    lane k), advances y = L^-1 b, and updates the trailing rows with the
-    column taken lane by lane;
-  - the draw: column-oriented back substitution of u = L^-T (y + z).
+  - the Cholesky: left-looking and in place on the bordered matrix (rows
+    0..K-1 Lambda*, row K b^T); in column k the lane of each row r >= k
+    subtracts the dot product of its row with row k, the pivot comes from
+    lane k; the bordered row is carried by lane K, or by lane 0 from column 1
+    on when K = 32 (lane 0 scales its column-0 entry right after the pivot);
+  - the draw: column-oriented back substitution of u = L^-T (y + z), y the
+    factor's row K.
 These tests check that the lane blocks cover the square exactly once for
-every padding width, and that the column order of operations gives the
-textbook draw u = mu* + L^-T z (mu* = Lambda*^-1 b) for every K it serves.
+every padding width, that every row of every column is computed by exactly
+one lane, and that this order of operations gives the textbook draw
+u = mu* + L^-T z (mu* = Lambda*^-1 b) for every K the kernel serves.
 """
 import numpy as np
 import pytest
@@ -49,29 +53,53 @@ def warp_gram(X, r, KP):
     return G[:K, :K], G[:K, K]
 
 
-def warp_draw(A, b, z):
-    """Right-looking column Cholesky with the forward solve, lane i = row i,
-    then the column-oriented back substitution."""
+def row_of_lane(i, k, K):
+    """The row lane i works on in column k (-1: none), as in the kernel."""
+    if i < K and i >= k:
+        return i
+    if (K == 32 and i == 0 and k >= 1) or (K < 32 and i == K):
+        return K
+    return -1
+
+
+def warp_draw(A, b, z, carry=True):
+    """Left-looking factorisation of the bordered matrix, lane by lane, then
+    the column-oriented back substitution (carry=False drops lane 0's scaling
+    of the bordered row's column-0 entry, for the control below)."""
     K = len(b)
-    x = np.tril(A).copy()  # lane i: x[i, :i + 1]
-    bi = b.copy()
+    M = np.zeros((K + 1, K + 1))
+    M[:K, :K] = np.tril(A)
+    M[K, :K] = b
     rinv = np.zeros(K)
     for k in range(K):
-        rs = 1.0 / np.sqrt(x[k, k])
-        x[k, k] *= rs
+        s = {}
+        for i in range(32):
+            r = row_of_lane(i, k, K)
+            if r >= 0:
+                s[r] = M[r, k] - M[r, :k] @ M[k, :k]
+        rs = 1.0 / np.sqrt(s[k])
+        for r, v in s.items():
+            M[r, k] = v * rs
+        M[k, k] = s[k] * rs
         rinv[k] = rs
-        x[k + 1:, k] *= rs
-        yk = bi[k] * rs
-        bi[k + 1:] -= x[k + 1:, k] * yk
-        bi[k] = yk
-        for j in range(k + 1, K):
-            x[j:, j] -= x[j:, k] * x[j, k]  # lanes i >= j take L[j][k] from lane j
-    w = bi + z
+        if K == 32 and k == 0 and carry:
+            M[K, 0] *= rs
+    L, y = M[:K, :K], M[K, :K]
+    w = y + z
     for k in range(K - 1, -1, -1):
         xk = w[k] * rinv[k]
         w[k] = xk
-        w[:k] -= x[k, :k] * xk
+        w[:k] -= L[k, :k] * xk
     return w
+
+
+@pytest.mark.parametrize("K", [1, 5, 16, 31, 32])
+def test_every_row_of_every_column_has_one_lane(K):
+    for k in range(K):
+        rows = [row_of_lane(i, k, K) for i in range(32)]
+        rows = [r for r in rows if r >= 0]
+        want = list(range(k, K)) + ([K] if (K < 32 or k >= 1) else [])
+        assert sorted(rows) == want
 
 
 @pytest.mark.parametrize("K", [1, 5, 8, 10, 16, 17, 31, 32])
@@ -95,21 +123,14 @@ def test_warp_draw_is_the_textbook_draw(K):
     assert np.allclose(u, ref, rtol=1e-10, atol=1e-12)
 
 
-def test_a_transposed_column_broadcast_is_caught():
-    """Control: taking L[k][j] instead of L[j][k] in the trailing update (the
-    transposed operand) breaks the draw."""
+def test_a_dropped_row_k_carry_is_caught():
+    """Control: without lane 0 scaling the bordered row's column-0 entry when
+    K = 32 (the one entry no lane computes in the loop), the draw is wrong."""
     rng = np.random.default_rng(3)
-    K = 12
-    X = 0.3 * rng.normal(size=(40, K))
+    K = 32
+    X = 0.3 * rng.normal(size=(90, K))
     A = np.eye(K) + 2.0 * X.T @ X
     b, z = rng.normal(size=K), rng.normal(size=K)
-    x = np.tril(A).copy()
-    for k in range(K):
-        rs = 1.0 / np.sqrt(x[k, k])
-        x[k, k] *= rs
-        x[k + 1:, k] *= rs
-        for j in range(k + 1, K):
-            x[j:, j] -= x[j:, k] * x[k, j]  # wrong operand (upper, zero)
-    assert not np.allclose(np.tril(x) @ np.tril(x).T, A)
-    assert np.allclose(warp_draw(A, b, z),
-                       np.linalg.solve(A, b) + np.linalg.solve(np.linalg.cholesky(A).T, z))
+    ref = np.linalg.solve(A, b) + np.linalg.solve(np.linalg.cholesky(A).T, z)
+    assert np.allclose(warp_draw(A, b, z), ref)
+    assert not np.allclose(warp_draw(A, b, z, carry=False), ref)
