@@ -91,8 +91,9 @@ typedef struct {
                          per row); heavier rows take the heavy-row kernel (tensor-core Gram
                          on MIXED, FP32 CTA per row on BINNED); -1: automatic */
   int32_t hub_min;    /* rows with degree >= hub_min are split across CTAs; -1: automatic */
-  int32_t tiny_max;   /* rows with degree <= tiny_max take the rank-one kernel (BINNED and
-                         MIXED paths); -1: automatic */
+  int32_t tiny_max;   /* rows with degree <= tiny_max take the tiny-row kernel, built from
+                         chol(Lambda_s) and one rank-one term per rating (BINNED and MIXED
+                         paths); -1 .. 32, -1: automatic */
   int32_t heavy_kernel; /* heavy rows on the MIXED path: 0 automatic (autotuned, else the
                            persistent warp-specialised kernel), 1 persistent kernel, 2 one CTA
                            per row with the Cholesky on tensor cores */
@@ -222,8 +223,8 @@ BPMF_API int bpmf_get_structure(bpmf_t *h, int side, int64_t *ptr, int32_t *idx,
 BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
 
 /* Work counters of `side`: rows per degree bin [tiny, light, heavy, hub]
- * (tiny: degree <= tiny_max, rank-one updates of chol(Lambda_s), one warp
- * per row; light: degree <= light_max, FP32 Gram, one warp per row for
+ * (tiny: degree <= tiny_max, chol(Lambda_s) and one rank-one term per
+ * rating, one warp per row; light: degree <= light_max, FP32 Gram, one warp per row for
  * K <= 32, else one CTA per row; heavy: tensor-core Gram on the MIXED path,
  * FP32 CTA per row on BINNED; hub: degree >= hub_min, split across
  * CTAs) and the number of rows the last sweep redid in FP64 (paper Sec. IV-B:
@@ -245,7 +246,7 @@ BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[5]);
  * and meaning (host array, read only during the call), e.g. ones the
  * autotuner chose in an earlier process: rows are re-binned by degree (the
  * degree bins and hub splitting of paper Sec. IV-B) and the next step
- * re-captures its graph.  tiny_max and light_max >= -1, hub_min >= 1; the
+ * re-captures its graph.  tiny_max -1 .. 32, light_max >= -1, hub_min >= 1; the
  * kernel [3] must be one the path and K can run (what bpmf_get_thresholds
  * could report: 1 or 2 on the MIXED path where supported, else 0), the
  * consumer count [4] 0 (automatic) .. 16 with kernel 1 (more than fit in

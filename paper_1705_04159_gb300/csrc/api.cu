@@ -55,7 +55,7 @@ void free_handle(Handle* h) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhi);
     dfree(sd.Xlo); dfree(sd.work);
-    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.lchol); dfree(sd.xbar); dfree(sd.S);
+    dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.lchol); dfree(sd.linvT); dfree(sd.xbar); dfree(sd.S);
     dfree(sd.piece_row); dfree(sd.piece_e0); dfree(sd.piece_e1); dfree(sd.hub_piece0);
   }
   dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
@@ -294,7 +294,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       !(cfg->nu0 > (double)K - 1.0) || !isfinite(cfg->nu0) || !(cfg->pivot_rel >= 0.0) ||
       !(cfg->pivot_rel < 1.0) || cfg->path < BPMF_PATH_PLAIN ||
       cfg->path > BPMF_PATH_MIXED || (cfg->order != 0 && cfg->order != 1) || cfg->burnin < 0 ||
-      cfg->heavy_kernel < 0 || cfg->heavy_kernel > 2) {
+      cfg->heavy_kernel < 0 || cfg->heavy_kernel > 2 || cfg->tiny_max > kTinyDegreeMax) {
     set_error("bpmf_init: invalid shape or configuration (K=%d M=%lld N=%lld nnz=%lld)", K,
               (long long)M, (long long)N, (long long)nnz);
     return BPMF_EINVAL;
@@ -335,6 +335,10 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       if ((rc = dalloc(&sd.mu, K))) break;
       if ((rc = dalloc(&sd.lamaug, (int64_t)(K + 1) * (K + 1)))) break;
       if ((rc = dalloc(&sd.lchol, KK))) break;
+      {
+        const int64_t KP = (K + 31) & ~31;
+        if ((rc = dalloc(&sd.linvT, KP * (KP + 1)))) break;
+      }
       if (cfg->path == BPMF_PATH_MIXED) {
         sd.KS = (K + 7) & ~7;
         if ((rc = dalloc(&sd.Xhi, sd.R * sd.KS))) break;

@@ -77,7 +77,7 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   }
   r.row_begin = e_light;
   r.row_end = sd.R;
-  return launch_rows_rank1(r, sd.lchol, st, &h->kernels);
+  return launch_rows_rank1(r, sd.lchol, sd.linvT, (int)sd.tiny_max, st, &h->kernels);
 }
 
 namespace {
@@ -207,7 +207,8 @@ int setup_bins(Handle* h, int s) {
 // an earlier process.  The kernel must be one this path and K can run.
 int set_thresholds(Handle* h, int s, const int64_t t[5]) {
   SideDev& sd = h->side[s];
-  if (t[0] < -1 || t[1] < -1 || t[2] < 1 || t[4] < 0 || t[4] > 16) return BPMF_EINVAL;
+  if (t[0] < -1 || t[0] > kTinyDegreeMax || t[1] < -1 || t[2] < 1 || t[4] < 0 || t[4] > 16)
+    return BPMF_EINVAL;
   const bool mixed = h->cfg.path == BPMF_PATH_MIXED;
   const bool can_ws = mixed && sd.Xhi && ws_supported(h->K);
   const bool can_tc = mixed && tc_supported(h->K);
@@ -387,7 +388,7 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     const int64_t light = sd.light_max;
     int64_t best_v = sd.tiny_max;
     float best = 3.0e38f;
-    for (int64_t v : distinct_cuts(sd, {-1, 0, 1, 2, 4, 8, 16, 32, 64})) {
+    for (int64_t v : distinct_cuts(sd, {-1, 0, 1, 2, 4, 8, 16, 32})) {
       // a tiny threshold above light_max moves light rows (and the boundary)
       BPMF_TRY(apply_bins(h, s, v, std::max(light, v), sd.hub_min));
       BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));

@@ -19,6 +19,8 @@
 namespace gb {
 
 constexpr int kMaxK = 128;
+// largest degree the tiny-row kernel takes (its per-warp buffers grow with it)
+constexpr int kTinyDegreeMax = 32;
 constexpr int kGammaCap = 64;                   // Gamma rejection attempts per draw
 constexpr uint64_t kWaitNsDefault = 2000000000ull;  // 2 s bound per pipeline wait
 
@@ -54,6 +56,7 @@ struct SideDev {
   double* mu = nullptr;    // K
   float* lamaug = nullptr; // (K+1)^2: Lambda_s bordered by b0 = Lambda_s mu_s (row and column K)
   float* lchol = nullptr;  // K(K+1)/2: chol(Lambda_s), lower, packed by rows, FP32 (rank-one kernel)
+  float* linvT = nullptr;  // KP x (KP + 1), KP = K rounded up to 32: (L_s^-1)^T (tiny-row kernel)
   // split rows (hubs): pieces of at most kPiece ratings, in degree order
   int64_t n_hub = 0, n_pieces = 0;
   int32_t* piece_row = nullptr;     // [n_pieces] row id

@@ -69,6 +69,9 @@ int ws_stage_neighbours(int64_t nnz, int64_t R);
 bool warp_supported(int K);
 int launch_rows_warp(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
-int launch_rows_rank1(const SweepArgs& a, const float* lchol, cudaStream_t st, int64_t* launches);
+// rows of degree <= max_degree (<= kTinyDegreeMax) from chol(Lambda_s); linvT is
+// scratch of KP x (KP + 1) floats that the call fills with (L_s^-1)^T first
+int launch_rows_rank1(const SweepArgs& a, const float* lchol, float* linvT, int max_degree,
+                      cudaStream_t st, int64_t* launches);
 
 }  // namespace gb

@@ -164,7 +164,7 @@ def test_missing_library_fails_loudly():
 @pytest.mark.parametrize("field,value", [
     ("alpha", 0.0), ("alpha", -1.0), ("alpha", float("nan")), ("alpha", float("inf")),
     ("beta0", float("inf")), ("beta0", 0.0), ("nu0", float("nan")), ("nu0", float("inf")),
-    ("pivot_rel", 1.0), ("pivot_rel", -0.1), ("pivot_rel", float("nan")),
+    ("pivot_rel", 1.0), ("pivot_rel", -0.1), ("pivot_rel", float("nan")), ("tiny_max", 33),
 ])
 def test_init_rejects_non_positive_or_non_finite_settings(libpath, field, value):
     """The row precision Lambda_s + alpha sum v v^T is positive definite for

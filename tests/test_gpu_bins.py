@@ -1,11 +1,11 @@
-"""Degree bins against the oracle: the rank-one kernel for rows with few
+"""Degree bins against the oracle: the tiny-row kernel for rows with few
 ratings, the FP32 light bin beside the tensor-core heavy bin, and the
 threshold autotuner.
 
-The rank-one kernel reaches chol(Lambda_s + alpha sum_j v_j v_j^T) from
-chol(Lambda_s) by one update per rating; the factor is unique, so its draws
-must match the oracle's (which factorises from scratch) to the FP32
-tolerance.
+The tiny-row kernel reaches the factor of Lambda_s + alpha sum_j v_j v_j^T
+from chol(Lambda_s) and one rank-one term per rating, without forming it;
+the factor is unique, so its draws must match the oracle's (which factorises
+from scratch) to the FP32 tolerance.
 """
 import numpy as np
 import pytest
@@ -42,8 +42,9 @@ def _sampler(bp, ds, K, path, seed=0, **kw):
 
 
 @pytest.mark.parametrize("name,tiny_max", [
-    ("chembl_like_k64", 8), ("tiny_k10", 16), ("uniform_k7", 1000), ("powerlaw_k33", 16),
-    ("powerlaw_k100", 16), ("powerlaw_k128", 8), ("uniform_k119", 64), ("chembl_like_k64", 0),
+    ("chembl_like_k64", 8), ("tiny_k10", 16), ("uniform_k7", 32), ("powerlaw_k33", 16),
+    ("powerlaw_k100", 16), ("powerlaw_k128", 8), ("uniform_k119", 32), ("chembl_like_k64", 0),
+    ("powerlaw_k128", 32), ("chembl_like_k64", 1),
 ])
 @pytest.mark.parametrize("path", ["binned", "mixed"])
 def test_rank_one_rows_parity(gpu_lib, name, tiny_max, path):
@@ -71,13 +72,13 @@ def test_rank_one_rows_parity(gpu_lib, name, tiny_max, path):
 
 
 def test_rank_one_rows_alone_match_full_factorisation_rows(gpu_lib):
-    """Every row through the rank-one kernel against every row through the
-    FP32 CTA kernel: the same draws to FP32 rounding."""
+    """Every user through the tiny-row kernel (at most 20 ratings each) against
+    every user through the FP32 CTA kernel: the same draws to FP32 rounding."""
     bp = gpu_lib
     ds, K, _ = _case("uniform_k7")
     U, V, _, hyper = random_state(ds, K)
     outs = []
-    for tiny in (-1, 10 ** 6):
+    for tiny in (-1, 32):
         with _sampler(bp, ds, K, bp.PATH_BINNED, seed=3, tiny_max=tiny) as s:
             bins, _ = s.sweep_info(0)
             assert (bins[0] == ds.M) == (tiny > 0)
@@ -159,7 +160,7 @@ def test_set_thresholds_reproduces_a_tuned_schedule(gpu_lib):
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
         before = plain.thresholds(0)
         for bad in ((-2, 0, 8192, 1, 0), (0, 0, 0, 1, 0), (0, 0, 8192, 0, 0), (0, 0, 8192, 2, 3),
-                    (0, 0, 8192, 1, 17)):
+                    (0, 0, 8192, 1, 17), (33, 33, 8192, 1, 0)):
             with pytest.raises(bp.BpmfError):
                 plain.set_thresholds(0, bad)
             assert plain.thresholds(0) == before

@@ -23,7 +23,9 @@ pytestmark = pytest.mark.gpu
 BIG = 1 << 30
 # name: (K, path, sampler keywords)
 CASES = {
-    "rank_one": (16, "binned", dict(tiny_max=BIG, light_max=BIG, hub_min=BIG)),
+    # the ill-conditioned users have 2K = 32 ratings: the tiny-row kernel's
+    # largest degree; the others (64) take the light bin
+    "rank_one": (16, "binned", dict(tiny_max=32, light_max=BIG, hub_min=BIG)),
     "fp32_cta_k16": (16, "binned", dict(tiny_max=-1, light_max=BIG, hub_min=BIG)),
     "fp32_cta_k64": (64, "binned", dict(tiny_max=-1, light_max=BIG, hub_min=BIG)),
     "hub_pieces": (16, "binned", dict(tiny_max=-1, light_max=BIG, hub_min=32)),
@@ -49,7 +51,7 @@ def test_ill_conditioned_rows_are_redone_in_fp64(gpu_lib, name):
     with bp.Sampler(ds.M, ds.N, ds.train_row, ds.train_col, ds.train_val, K=K, alpha=ds.alpha,
                     seed=seed, path=pmap[path], **kw) as s:
         if path == "binned" and name.startswith("rank"):
-            assert s.sweep_info(0)[0][0] == ds.M  # every user in the rank-one bin
+            assert s.sweep_info(0)[0][0] == len(bad)  # the ill-conditioned users, tiny bin
         s.set_state(U, V, hyper, it=it)
         s.sweep(0)
         redone = s.sweep_info(0)[1]
