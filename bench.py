@@ -47,7 +47,13 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (2 flop each per cloc
 # case and kernel version they were taken on; keyed by (workload, side,
 # heavy kernel, consumer warps).  A capture of a smaller case is scaled to the
 # full launch by ratings (the per-rating index and value reads dominate).
-TRAFFIC = {}
+TRAFFIC = {
+    ("netflix", 0, 1, 6): (
+        (165.3e6 + 27.7e6) * 5,
+        "ncu dram__bytes_read + dram__bytes_write of the users launch with this schedule (six "
+        "consumers) on the 120,000 x 17,770 case with 18M training ratings, 193 MB, scaled x5 "
+        "by ratings to this launch (profiles/row_ws_powerlaw120k_k100.md)"),
+}
 
 
 def fp32_peak_from(sms, sm_mhz):
