@@ -373,6 +373,7 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.Vhi = od.Xhi;
   a.Vlo = od.Xlo;
   a.KS = od.KS;
+  a.n_other = od.R;
   return a;
 }
 

@@ -39,6 +39,7 @@ struct SweepArgs {
   const __nv_bfloat16* Vhi;
   const __nv_bfloat16* Vlo;
   int KS;
+  int64_t n_other;      // rows of the other side (of Vo and its shadow)
   // per slot of the degree order: (row, first rating, one past the last, 0)
   const int4* work;
   float* wsbase;        // base tiles of the persistent kernel (rows_ws.cu)

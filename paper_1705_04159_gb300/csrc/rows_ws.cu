@@ -11,10 +11,10 @@
 // (largest first) and runs them through a pipeline of warp roles:
 //   gather (warps 0-3): copies the bf16 hi/lo shadow rows of the neighbours,
 //     NB per stage (32, or 64 on a side whose rows average 256 or more
-//     ratings), with 16-byte cp.async straight into MN-major operand tiles
-//     (feature-contiguous 8 x 16-byte core matrices: chunk c of neighbour k
-//     at c * 16 NB + (k / 8) * 128 + (k % 8) * 16) into a ring of stages, and
-//     patches the rating in as feature K;
+//     ratings), by tensor-memory-accelerator gather4 copies (four neighbour
+//     rows x 64 features each) straight into MN-major operand tiles with the
+//     128-byte swizzle, into a ring of stages, and patches the rating in as
+//     feature K;
 //   MMA (warp 8, one thread): per 16 neighbours hi.hi + hi.lo + lo.hi into
 //     one of two FP32 accumulators in tensor memory (G = X^T X with X the
 //     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped);
@@ -38,6 +38,9 @@
 
 #include <algorithm>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "bpmf_impl.cuh"
 #include "rows.cuh"
 #include "tc_ptx.cuh"
@@ -46,17 +49,24 @@
 namespace gb {
 namespace {
 
-constexpr int kWsLBO = 128;          // operand tiles: bytes between 8-neighbour groups
+// Operand tiles (hi and lo, one each per stage) are MN-major with the
+// 128-byte swizzle: neighbour k of the stage is a 128-byte row of 64 features
+// (row k % 8 of the 1024-byte atom of 8-neighbour group k / 8), features
+// 64 .. 127 in a second block of atoms NB * 128 bytes further; within each
+// row the 16-byte chunk c sits at position c ^ (k % 8).  This is the layout
+// the tensor memory accelerator writes for a box of 64 bf16 with the
+// 128-byte swizzle, so one gather4 fills four neighbour rows of one block.
+constexpr int kWsAtom = 1024;        // 8 neighbour rows x 128 bytes
 constexpr int64_t kWsLongRow = 256;  // mean ratings per row from which stages hold 64 neighbours
 // Neighbours per stage NB: 32 (two MMA K-steps) or 64 (four), chosen per side:
 // bigger stages halve the hand-offs per neighbour where rows are long.
 template <int NB>
 struct WsNb {
-  static constexpr int kSBO = NB * 16;              // bytes between 8-feature chunks
-  static constexpr int kOpBytes = 16 * kSBO;        // 128 features (the MMA reads M = 128 rows)
+  static constexpr int kBlk = NB * 128;             // bytes of one 64-feature block
+  static constexpr int kOpBytes = 2 * kBlk;         // 128 features (the MMA reads M = 128 rows)
   static constexpr int kStageBytes = 2 * kOpBytes;  // hi + lo
 };
-__host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 16 * nb * 16; }
+__host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 2 * nb * 128; }
 constexpr int kWsMaxStages = 16;
 constexpr int kWsMaxCons = 7;
 constexpr int kWsRecs = 32;          // row records in flight: >= stages + 3 (see the gather loop)
@@ -127,6 +137,7 @@ struct WsShared {
   uint16_t* sched;  // [32 * nround] lane units, then [g + 1] first round of each panel
   uint64_t* full;
   uint64_t* empty;
+  uint64_t* tma;  // the stage's gather4 copies have landed
   uint64_t* acc_full;
   uint64_t* acc_empty;
   uint64_t* slot_full;
@@ -143,17 +154,19 @@ struct WsShared {
   uint64_t wait_ns;  // bound of every pipeline wait (SweepArgs::wait_ns)
 };
 
-// mbarriers: full and empty per stage, full and empty per accumulator, full
-// and empty per consumer slot, fin, row_ready, row_read (an even count, so
-// that what follows stays 16-byte aligned)
-__host__ __device__ inline int ws_nbar(int S, int C) { return (2 * S + 4 + 2 * C + 3 + 1) & ~1; }
+// mbarriers: full, empty and tma per stage, full and empty per accumulator,
+// full and empty per consumer slot, fin, row_ready, row_read (an even count,
+// so that what follows stays 16-byte aligned)
+__host__ __device__ inline int ws_nbar(int S, int C) { return (3 * S + 4 + 2 * C + 3 + 1) & ~1; }
 __host__ __device__ inline int ws_fixed_bytes(int nb, int S, int C) {
   // barriers, stage meta, row records, ratings, next_row, abort, taddr
   return 8 * ws_nbar(S, C) + 16 * S + 16 * kWsRecs + 4 * S * nb + 32;
 }
-// stages, consumer slots, the trailing-update schedule, then the fixed part
+// stages, consumer slots, the trailing-update schedule, then the fixed part;
+// one atom more, to start the stages on a 1024-byte boundary (the swizzle
+// pattern follows address bits 7 .. 9)
 __host__ __device__ inline int ws_smem_bytes(const WsGeom& G, int S, int C, int nb) {
-  return S * ws_stage_bytes(nb) + C * G.slot_floats() * 4 + G.sched_bytes() +
+  return kWsAtom + S * ws_stage_bytes(nb) + C * G.slot_floats() * 4 + G.sched_bytes() +
          ws_fixed_bytes(nb, S, C);
 }
 
@@ -166,7 +179,8 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
   w.full = b;
   w.empty = b + S;
-  w.acc_full = b + 2 * S;
+  w.tma = b + 2 * S;
+  w.acc_full = b + 3 * S;
   w.acc_empty = w.acc_full + 2;
   w.slot_full = w.acc_empty + 2;
   w.slot_empty = w.slot_full + C;
@@ -223,18 +237,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// 16-byte copy into shared memory through L2 only (.cg): the neighbour rows
-// have little reuse within one SM, and leaving L1 to the drain's base tiles
-// keeps those resident
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+// Waits (bounded, whatever the abort flag and the pipeline bound say) until
+// copies this warp issued have landed: shared memory must not be written
+// after the block ends.  Copies land within microseconds; the 2 s bound only
+// keeps the wait finite.
+constexpr uint64_t kWsCopyDrainNs = 2000000000ull;
+__device__ __forceinline__ void ws_wait_copies(uint64_t* bar, uint32_t parity, uint64_t limit) {
+  const uint64_t t0 = ws_gtimer();
+  while (!mbar_try_wait(bar, parity) && ws_gtimer() - t0 < limit) {
+  }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 
 // kind::f16 instruction descriptor, BF16 operands both MN-major (bits 15, 16).
 __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
@@ -244,38 +256,66 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
 // ------------------------------------------------------------- gather --
 // The four gather warps take the stages of the row sequence in turn (stage n
 // by warp n % 4), so four stages are filled side by side.  In the warp that
-// fills stage n, lane l handles neighbours l, l + 32, .. (NB / 32 of them) and
-// every chunk c of each, so the warp writes chunk c of 32 neighbours as 512
-// contiguous bytes.  Chunks 0 .. ceil(K/8) - 1 are 16-byte copies of the
-// shadow row (its padding past K is zero); the rating (feature K, in chunk
-// cb = K / 8) is patched in once the copy of its chunk has landed
-// (ws_patch_rating).  Rows k >= cnt are zeroed.
+// fills stage n, lane l holds neighbours l, l + 32, .. (NB / 32 of them);
+// lane g < 4 ceil(cnt / 16) copies the rows of neighbours 4g .. 4g + 3 into
+// both operand tiles with one gather4 per 64-feature block and tile.  Rows
+// past cnt (up to the MMA's 16-neighbour step) are read at an out-of-range
+// row index, which the copy fills with zeros.  The rating (feature K) is
+// patched in once the copies have landed (ws_patch_rating).
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int x, int y0,
+                                            int y1, int y2, int y3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
 template <int NB>
-__device__ __forceinline__ void ws_gather_stage(const WsGeom& G, const SweepArgs& a,
-                                                uint8_t* stage, int cnt, int32_t j, int k) {
-  const bool live = k < cnt;
-  const __nv_bfloat16* hrow = a.Vhi + (int64_t)j * a.KS;
-  const __nv_bfloat16* lrow = a.Vlo + (int64_t)j * a.KS;
-  const uint32_t hi = smem_u32(stage), lo = hi + WsNb<NB>::kOpBytes;
-  const int koff = (k >> 3) * kWsLBO + (k & 7) * 16;
-  const int ncopy = (G.K + 7) >> 3;
-  for (int c = 0; c <= G.cb; ++c) {
-    const int off = c * WsNb<NB>::kSBO + koff;
-    if (live && c < ncopy) {
-      cp_async16(hi + off, hrow + 8 * c);
-      cp_async16(lo + off, lrow + 8 * c);
-    } else {
-      *reinterpret_cast<uint4*>(stage + off) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(stage + WsNb<NB>::kOpBytes + off) = make_uint4(0, 0, 0, 0);
+__device__ __forceinline__ void ws_issue_stage(const WsGeom& G, const SweepArgs& a,
+                                               const CUtensorMap* map_hi, const CUtensorMap* map_lo,
+                                               uint8_t* stage, uint64_t* bar, int cnt,
+                                               const int32_t (&j)[NB / 32], int lane) {
+  const int ngroups = 4 * ((cnt + 15) >> 4);
+  const int nblk = G.KA > 64 ? 2 : 1;
+  // ids of neighbours 4 lane .. 4 lane + 3 (out of range past cnt)
+  int y[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = 4 * lane + i;
+    int v = 0;
+#pragma unroll
+    for (int u = 0; u < NB / 32; ++u) {
+      const int t = __shfl_sync(0xffffffffu, j[u], k & 31);
+      if ((k >> 5) == u) v = t;
+    }
+    y[i] = k < cnt ? v : (int)a.n_other;
+  }
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(ngroups * nblk * 2 * 512));
+  __syncwarp();
+  if (lane < ngroups) {
+    const uint32_t hi = smem_u32(stage) + (uint32_t)((lane >> 1) * kWsAtom + (lane & 1) * 512);
+    for (int b = 0; b < nblk; ++b) {
+      const uint32_t off = (uint32_t)(b * WsNb<NB>::kBlk);
+      tma_gather4(hi + off, map_hi, 64 * b, y[0], y[1], y[2], y[3], bar);
+      tma_gather4(hi + WsNb<NB>::kOpBytes + off, map_lo, 64 * b, y[0], y[1], y[2], y[3], bar);
     }
   }
 }
 
-// Feature K of neighbour k = the rating r, as bf16 hi and lo, written by the
-// lane that copied chunk cb of that neighbour, after its copy completed.
+// Feature K of neighbour k = the rating r, as bf16 hi and lo, at its
+// swizzled place in the operand tiles.
 template <int NB>
 __device__ __forceinline__ void ws_patch_rating(const WsGeom& G, uint8_t* stage, float r, int k) {
-  const int off = G.cb * WsNb<NB>::kSBO + (k >> 3) * kWsLBO + (k & 7) * 16 + 2 * (G.K & 7);
+  const int f = G.K, k0 = k & 7;
+  const int off = (f >> 6) * WsNb<NB>::kBlk + (k >> 3) * kWsAtom + k0 * 128 +
+                  ((((f >> 3) & 7) ^ k0) << 4) + 2 * (f & 7);
   const __nv_bfloat16 h = __float2bfloat16_rn(r);
   *reinterpret_cast<__nv_bfloat16*>(stage + off) = h;
   *reinterpret_cast<__nv_bfloat16*>(stage + WsNb<NB>::kOpBytes + off) =
@@ -291,22 +331,26 @@ __host__ __device__ __forceinline__ int ws_slot(uint32_t n, int S) {
 }
 
 // Copies of a warp's previous stage are waited for, patched, made visible to
-// the tensor cores and signalled once its next stage has been issued.
+// the tensor cores and signalled once its next stage has been issued.  False
+// if the wait ran out (abort is set; the stage is not signalled).
 template <int NB>
-__device__ __forceinline__ void ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
+__device__ __forceinline__ bool ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
                                           int lane) {
   const int ss = ws_slot(m, S);
+  if (!ws_wait_warp(&w.tma[ss], (m / (uint32_t)S) & 1u, w.abort, w.wait_ns)) return false;
 #pragma unroll
   for (int t = 0; t < NB / 32; ++t)
     ws_patch_rating<NB>(G, w.stages + ss * WsNb<NB>::kStageBytes, w.rating[ss * NB + lane + 32 * t],
                         lane + 32 * t);
   fence_proxy_async_smem();
   mbar_arrive(&w.full[ss]);
+  return true;
 }
 
 template <int NB>
 __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
-                                          int S, int* counter) {
+                                          int S, int* counter, const CUtensorMap* map_hi,
+                                          const CUtensorMap* map_lo) {
   constexpr int NL = NB / 32;  // neighbours per lane
   const int t = threadIdx.x;
   const int wg = t >> 5, lane = t & 31;
@@ -317,7 +361,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   const int lag = S / 4 - 1 < 3 ? S / 4 - 1 : 3;
   uint32_t n = 0;             // stage sequence number (the same in every gather warp)
   int q = 0;                  // row sequence number
-  uint32_t pend[3] = {0u, 0u, 0u};  // this warp's issued stages not yet signalled, oldest first
+  uint32_t pend[4] = {0u, 0u, 0u, 0u};  // this warp's issued stages not yet signalled, oldest first
   int npend = 0;
   // thread 0 prefetches the next row's work entry (row, first, last rating)
   int4 wk = make_int4(-1, 0, 0, 0);
@@ -394,40 +438,42 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
 #pragma unroll
       for (int u = 0; u < NL; ++u) {
         const int k = lane + 32 * u;
-        if (cnt > 0) ws_gather_stage<NB>(G, a, w.stages + s * WsNb<NB>::kStageBytes, cnt, j[u], k);
         w.rating[s * NB + k] = k < cnt ? r[u] : 0.f;
       }
-      cp_async_commit();
-      if (npend == lag) {
-        // the oldest of lag + 1 outstanding copy groups has landed once at
-        // most lag remain
-        if (lag == 0) cp_async_wait<0>();
-        else if (lag == 1) cp_async_wait<1>();
-        else if (lag == 2) cp_async_wait<2>();
-        else cp_async_wait<3>();
-        if (lag == 0) {
-          ws_signal<NB>(G, w, S, nn, lane);
-        } else {
-          ws_signal<NB>(G, w, S, pend[0], lane);
-          pend[0] = lag > 1 ? pend[1] : nn;
-          pend[1] = lag > 2 ? pend[2] : nn;
-          pend[2] = nn;
+      ws_issue_stage<NB>(G, a, map_hi, map_lo, w.stages + s * WsNb<NB>::kStageBytes, &w.tma[s], cnt,
+                         j, lane);
+      pend[0] = npend == 0 ? nn : pend[0];
+      pend[1] = npend == 1 ? nn : pend[1];
+      pend[2] = npend == 2 ? nn : pend[2];
+      pend[3] = npend == 3 ? nn : pend[3];
+      ++npend;
+      if (npend > lag) {
+        // the oldest of lag + 1 issued stages: its copies are waited for,
+        // then it is patched and signalled
+        if (!ws_signal<NB>(G, w, S, pend[0], lane)) {
+          stop = true;
+          break;
         }
-      } else {
-        pend[0] = npend == 0 ? nn : pend[0];
-        pend[1] = npend == 1 ? nn : pend[1];
-        pend[2] = npend == 2 ? nn : pend[2];
-        ++npend;
+        pend[0] = pend[1];
+        pend[1] = pend[2];
+        pend[2] = pend[3];
+        --npend;
       }
     }
     n += (uint32_t)nst;
     if (stop || row < 0) break;
     ++q;
   }
-  cp_async_wait<0>();
+  // the stages still outstanding are signalled; after a wait that ran out,
+  // their copies are only waited for
+  bool failed = false;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if (i < npend) ws_signal<NB>(G, w, S, pend[i], lane);
+  for (int i = 0; i < 4; ++i)
+    if (i < npend) {
+      if (!failed) failed = !ws_signal<NB>(G, w, S, pend[i], lane);
+      if (failed)
+        ws_wait_copies(&w.tma[ws_slot(pend[i], S)], (pend[i] / (uint32_t)S) & 1u, kWsCopyDrainNs);
+    }
 }
 
 // ---------------------------------------------------------------- MMA --
@@ -451,10 +497,11 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
     const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
     if (m.cnt > 0) {
       const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
-      // K-steps of 16 neighbours: two 8-neighbour groups (2 LBO) apart
+      // K-steps of 16 neighbours: two atoms apart; the leading byte offset
+      // steps between 64-feature blocks, the stride one between atoms
       for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
-        const uint64_t dh = smem_desc_kmajor(hi + kk * 2 * kWsLBO, kWsLBO, WsNb<NB>::kSBO);
-        const uint64_t dl = smem_desc_kmajor(lo + kk * 2 * kWsLBO, kWsLBO, WsNb<NB>::kSBO);
+        const uint64_t dh = smem_desc_sw128(hi + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
+        const uint64_t dl = smem_desc_sw128(lo + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
         tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
         tc_mma_bf16(acc, dh, dl, idesc, 1u);
         tc_mma_bf16(acc, dl, dh, idesc, 1u);
@@ -792,17 +839,21 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
 }
 
 template <int NB>
-__global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C, int* counter,
-                                                 int* status) {
+__global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
+                                                 const __grid_constant__ CUtensorMap map_hi,
+                                                 const __grid_constant__ CUtensorMap map_lo, int S,
+                                                 int C, int* counter, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_ws[];
   const WsGeom G(a.K);
-  WsShared w = ws_carve(smem_ws, G, S, C, NB);
+  uint8_t* base = smem_ws + ((kWsAtom - (smem_u32(smem_ws) & (kWsAtom - 1))) & (kWsAtom - 1));
+  WsShared w = ws_carve(base, G, S, C, NB);
   w.wait_ns = a.wait_ns;
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&w.full[s], 32);  // the lanes of the warp that fills the stage
       mbar_init(&w.empty[s], 1);
+      mbar_init(&w.tma[s], 1);    // its lane 0's arrive with the bytes to expect
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&w.acc_full[b], 1);
@@ -818,7 +869,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
     *w.abort = 0;
     mbar_fence_init();
   }
-  // operand chunks past the last written one (features beyond K) stay zero
+  // operand blocks no copy writes (features 64 .. 127 when K + 1 <= 64) stay zero
   for (int e = threadIdx.x; e < S * WsNb<NB>::kStageBytes / 16; e += blockDim.x)
     reinterpret_cast<uint4*>(w.stages)[e] = make_uint4(0, 0, 0, 0);
   {  // this g's trailing-update schedule, rounds counted from its first
@@ -837,7 +888,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a, int S, int C
   tc_fence_after();
   const uint32_t tmem = *w.taddr;
   if (warp < 4) {
-    ws_gather<NB>(a, G, w, S, counter);
+    ws_gather<NB>(a, G, w, S, counter, &map_hi, &map_lo);
   } else if (warp < 8) {
     ws_drain(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
@@ -922,6 +973,51 @@ int ws_config(int K, int cons, int nb, int* S, int* C) {
   return BPMF_OK;
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled of the driver, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The other side's shadow (rows x KS bf16, rows 16-byte aligned) as a 2-D
+// tensor read in boxes of 64 features x 1 row (gather4 boxes are one row
+// high) with the 128-byte swizzle; rows and features past the end read as
+// zeros.
+int encode_shadow_map(const __nv_bfloat16* p, int64_t rows, int KS, CUtensorMap* map) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (enc == nullptr) {
+    set_error("row_ws: cuTensorMapEncodeTiled is not available");
+    return BPMF_ECUDA;
+  }
+  const cuuint64_t dim[2] = {(cuuint64_t)KS, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)KS * sizeof(__nv_bfloat16)};
+  const cuuint32_t box[2] = {64, 1};
+  const cuuint32_t step[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p),
+                         dim, stride, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("row_ws: tensor map of the shadow rejected (%d)", (int)r);
+    return BPMF_ECUDA;
+  }
+  return BPMF_OK;
+}
+
+}  // namespace
+
 int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* counter, int* status,
                    cudaStream_t st, int64_t* launches) {
   const int64_t nrows = a.row_end - a.row_begin;
@@ -938,7 +1034,10 @@ int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* count
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   const int grid = (int)std::min<int64_t>(num_sms, nrows);
-  kern<<<grid, 32 * ws_warps(C), smem, st>>>(a, S, C, counter, status);
+  CUtensorMap map_hi, map_lo;
+  BPMF_TRY(encode_shadow_map(a.Vhi, a.n_other, a.KS, &map_hi));
+  BPMF_TRY(encode_shadow_map(a.Vlo, a.n_other, a.KS, &map_lo));
+  kern<<<grid, 32 * ws_warps(C), smem, st>>>(a, map_hi, map_lo, S, C, counter, status);
   BPMF_CUDA_CHECK(cudaGetLastError());
   if (launches) *launches += 1;
   return BPMF_OK;

@@ -102,6 +102,15 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t addr, uint32_t lbo
   return d;                // base offset 0, absolute LBO mode, layout type 0 = no swizzle
 }
 
+// The same for operands in the 128-byte swizzled layout (layout type 2):
+// MN-major tiles of 8-row x 128-byte atoms whose 16-byte chunks are permuted
+// by the row within the atom.  For MN-major operands LBO is the byte step
+// between 64-element blocks along M (or N), SBO the step between 8-row atoms
+// along K; the atoms start on 1024-byte boundaries (base offset 0).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc_kmajor(addr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
 // K-major, no negation, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
