@@ -272,6 +272,16 @@ BPMF_API int bpmf_set_thresholds(bpmf_t *h, int side, const int64_t thresholds[5
  * The next bpmf_step re-records its graph.  Errors: EINVAL. */
 BPMF_API int bpmf_set_limits(bpmf_t *h, int32_t gamma_cap, int64_t wait_ns);
 
+/* Failure-path testing only (the paper has no counterpart).  hold = 1 makes
+ * the persistent row kernel of the following sweeps withhold the arrive that
+ * hands its first accumulator to the drain: that wait then runs out after
+ * wait_ns (bpmf_set_limits), every role of the kernel leaves as on any
+ * timeout, and the sweep returns BPMF_ECUDA with "timed out" in
+ * bpmf_last_error; the rows of such a sweep are undefined and the handle
+ * stays usable.  hold = 0 (the default) restores normal operation.  The next
+ * bpmf_step re-records its graph.  Errors: EINVAL. */
+BPMF_API int bpmf_set_test_hold(bpmf_t *h, int32_t hold);
+
 /* ---- kernel timers (bpmf_get_timing) ---- */
 #define BPMF_T_HYPER_REDUCE 0  /* factor mean and scatter reductions */
 #define BPMF_T_HYPER_DRAW 1    /* FP64 Normal-Wishart draw */

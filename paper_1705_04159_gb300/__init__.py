@@ -21,8 +21,8 @@ __all__ = [
     "bpmf_get_state", "bpmf_set_state", "bpmf_get_structure", "bpmf_get_hyper_stats",
     "bpmf_get_sweep_info", "bpmf_set_timing", "bpmf_get_timing", "bpmf_destroy", "bpmf_strerror",
     "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds", "bpmf_set_thresholds",
-    "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
-    "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
+    "bpmf_set_test_hold", "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll",
+    "bpmf_server_wait", "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
     "Sampler", "Server", "Job", "JobResult", "TIMERS",
     "USERS", "MOVIES", "PATH_PLAIN", "PATH_BINNED", "PATH_MIXED", "DEVPTR",
 ]
@@ -38,8 +38,8 @@ SYMBOLS = [
     "bpmf_get_structure", "bpmf_get_hyper_stats", "bpmf_get_sweep_info", "bpmf_destroy",
     "bpmf_strerror", "bpmf_last_error", "bpmf_set_timing", "bpmf_get_timing",
     "bpmf_hyper_stats_noalloc", "bpmf_set_graph", "bpmf_get_thresholds", "bpmf_set_thresholds",
-    "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll", "bpmf_server_wait",
-    "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
+    "bpmf_set_test_hold", "bpmf_server_create", "bpmf_server_submit", "bpmf_server_poll",
+    "bpmf_server_wait", "bpmf_server_stats", "bpmf_server_clock", "bpmf_server_destroy",
 ]
 TIMERS = ["hyper_reduce", "hyper_draw", "rows_users", "rows_movies", "fp64_redo", "predict"]
 
@@ -123,6 +123,7 @@ def lib():
         L.bpmf_set_timing.argtypes = [P, C.c_int]
         L.bpmf_set_graph.argtypes = [P, C.c_int]
         L.bpmf_set_limits.argtypes = [P, i32, i64]
+        L.bpmf_set_test_hold.argtypes = [P, i32]
         L.bpmf_get_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_set_thresholds.argtypes = [P, C.c_int, P]
         L.bpmf_get_timing.argtypes = [P, P, P, P]
@@ -344,6 +345,12 @@ def bpmf_set_limits(h, gamma_cap=-1, wait_ns=0):
     _check(lib().bpmf_set_limits(h, int(gamma_cap), int(wait_ns)), "bpmf_set_limits")
 
 
+def bpmf_set_test_hold(h, hold):
+    """Failure-path testing: 1 makes the persistent kernel withhold one
+    arrive, so that its bounded wait runs out; 0 restores normal operation."""
+    _check(lib().bpmf_set_test_hold(h, int(hold)), "bpmf_set_test_hold")
+
+
 def bpmf_get_timing(h):
     """({timer: ms}, {timer: phases}, kernels launched) since timing was enabled."""
     ms = np.zeros(len(TIMERS))
@@ -537,6 +544,9 @@ class Sampler:
 
     def set_limits(self, gamma_cap=-1, wait_ns=0):
         bpmf_set_limits(self.h, gamma_cap, wait_ns)
+
+    def set_test_hold(self, hold):
+        bpmf_set_test_hold(self.h, hold)
 
     def thresholds(self, side):
         return bpmf_get_thresholds(self.h, side)

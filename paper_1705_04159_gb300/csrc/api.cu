@@ -529,6 +529,14 @@ int bpmf_set_limits(bpmf_t* hh, int32_t gamma_cap, int64_t wait_ns) {
   return BPMF_OK;
 }
 
+int bpmf_set_test_hold(bpmf_t* hh, int32_t hold) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || (hold != 0 && hold != 1)) return einval("bpmf_set_test_hold");
+  drop_graph(h);
+  h->hold_arrive = hold;
+  return BPMF_OK;
+}
+
 int bpmf_set_graph(bpmf_t* hh, int enable) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return einval("bpmf_set_graph");

@@ -137,6 +137,7 @@ struct Handle {
   // failure-path limits (bpmf_set_limits)
   int gamma_cap = kGammaCap;
   uint64_t wait_ns = kWaitNsDefault;
+  int hold_arrive = 0;  // failure-path testing: the persistent kernel withholds one arrive
 };
 
 // Brackets one phase with two events when timing is on (api.cu).

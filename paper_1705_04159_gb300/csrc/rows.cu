@@ -363,6 +363,7 @@ SweepArgs make_sweep_args(Handle* h, int s) {
   a.flag_count = h->flag_count;
   a.pivot_rel = (float)h->cfg.pivot_rel;
   a.wait_ns = h->wait_ns;
+  a.hold_arrive = h->hold_arrive;
   a.piece_row = sd.piece_row;
   a.piece_e0 = sd.piece_e0;
   a.piece_e1 = sd.piece_e1;

@@ -28,6 +28,7 @@ struct SweepArgs {
   int32_t* flag_count;
   float pivot_rel;      // a pivot <= pivot_rel x its starting diagonal flags the row
   uint64_t wait_ns;     // bound of each pipeline wait of the persistent kernel
+  int hold_arrive;      // failure-path testing: withhold the first accumulator's hand-off
   // split rows: piece p covers ratings [piece_e0[p], piece_e1[p]) of piece_row[p];
   // hub h (slot h of the degree order) owns pieces [hub_piece0[h], hub_piece0[h+1])
   const int32_t* piece_row;

@@ -135,9 +135,8 @@ struct WsShared {
   uint8_t* stages;
   float* slots;
   uint16_t* sched;  // [32 * nround] lane units, then [g + 1] first round of each panel
-  uint64_t* full;
   uint64_t* empty;
-  uint64_t* tma;  // the stage's gather4 copies have landed
+  uint64_t* tma;  // the stage's copies have landed (and its metadata and ratings are written)
   uint64_t* acc_full;
   uint64_t* acc_empty;
   uint64_t* slot_full;
@@ -154,10 +153,10 @@ struct WsShared {
   uint64_t wait_ns;  // bound of every pipeline wait (SweepArgs::wait_ns)
 };
 
-// mbarriers: full, empty and tma per stage, full and empty per accumulator,
-// full and empty per consumer slot, fin, row_ready, row_read (an even count,
-// so that what follows stays 16-byte aligned)
-__host__ __device__ inline int ws_nbar(int S, int C) { return (3 * S + 4 + 2 * C + 3 + 1) & ~1; }
+// mbarriers: empty and tma per stage, full and empty per accumulator, full
+// and empty per consumer slot, fin, row_ready, row_read (an even count, so
+// that what follows stays 16-byte aligned)
+__host__ __device__ inline int ws_nbar(int S, int C) { return (2 * S + 4 + 2 * C + 3 + 1) & ~1; }
 __host__ __device__ inline int ws_fixed_bytes(int nb, int S, int C) {
   // barriers, stage meta, row records, ratings, next_row, abort, taddr
   return 8 * ws_nbar(S, C) + 16 * S + 16 * kWsRecs + 4 * S * nb + 32;
@@ -177,10 +176,9 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   w.sched = reinterpret_cast<uint16_t*>(w.slots + C * G.slot_floats());
   uint8_t* p = reinterpret_cast<uint8_t*>(w.sched) + G.sched_bytes();
   uint64_t* b = reinterpret_cast<uint64_t*>(p);
-  w.full = b;
-  w.empty = b + S;
-  w.tma = b + 2 * S;
-  w.acc_full = b + 3 * S;
+  w.empty = b;
+  w.tma = b + S;
+  w.acc_full = b + 2 * S;
   w.acc_empty = w.acc_full + 2;
   w.slot_full = w.acc_empty + 2;
   w.slot_empty = w.slot_full + C;
@@ -297,6 +295,9 @@ __device__ __forceinline__ void ws_issue_stage(const WsGeom& G, const SweepArgs&
     }
     y[i] = k < cnt ? v : (int)a.n_other;
   }
+  // the arrive (release) publishes the lanes' metadata and rating writes with
+  // the copies: the MMA warp waits for this barrier alone
+  __syncwarp();
   if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(ngroups * nblk * 2 * 512));
   __syncwarp();
   if (lane < ngroups) {
@@ -330,23 +331,6 @@ __host__ __device__ __forceinline__ int ws_slot(uint32_t n, int S) {
   return (int)(n & 3u) + 4 * (int)((n >> 2) % (uint32_t)(S >> 2));
 }
 
-// Copies of a warp's previous stage are waited for, patched, made visible to
-// the tensor cores and signalled once its next stage has been issued.  False
-// if the wait ran out (abort is set; the stage is not signalled).
-template <int NB>
-__device__ __forceinline__ bool ws_signal(const WsGeom& G, const WsShared& w, int S, uint32_t m,
-                                          int lane) {
-  const int ss = ws_slot(m, S);
-  if (!ws_wait_warp(&w.tma[ss], (m / (uint32_t)S) & 1u, w.abort, w.wait_ns)) return false;
-#pragma unroll
-  for (int t = 0; t < NB / 32; ++t)
-    ws_patch_rating<NB>(G, w.stages + ss * WsNb<NB>::kStageBytes, w.rating[ss * NB + lane + 32 * t],
-                        lane + 32 * t);
-  fence_proxy_async_smem();
-  mbar_arrive(&w.full[ss]);
-  return true;
-}
-
 template <int NB>
 __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, const WsShared& w,
                                           int S, int* counter, const CUtensorMap* map_hi,
@@ -355,14 +339,12 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
   const int t = threadIdx.x;
   const int wg = t >> 5, lane = t & 31;
   const int nrows = (int)(a.row_end - a.row_begin);
-  // a warp owns S / 4 ring slots and keeps that many of its stages in flight
-  // (up to four): the copies of the oldest are waited for only when a newer
-  // one has been issued
-  const int lag = S / 4 - 1 < 3 ? S / 4 - 1 : 3;
+  // a warp owns the S / 4 ring slots wg + 4 i; it only issues copies (the
+  // MMA warp waits for them), and keeps the last stage issued into each slot
+  // so that it can wait for those copies before the block ends
   uint32_t n = 0;             // stage sequence number (the same in every gather warp)
   int q = 0;                  // row sequence number
-  uint32_t pend[4] = {0u, 0u, 0u, 0u};  // this warp's issued stages not yet signalled, oldest first
-  int npend = 0;
+  uint32_t last[4] = {~0u, ~0u, ~0u, ~0u};
   // thread 0 prefetches the next row's work entry (row, first, last rating)
   int4 wk = make_int4(-1, 0, 0, 0);
   int next_slot = 0;
@@ -442,84 +424,86 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
       }
       ws_issue_stage<NB>(G, a, map_hi, map_lo, w.stages + s * WsNb<NB>::kStageBytes, &w.tma[s], cnt,
                          j, lane);
-      pend[0] = npend == 0 ? nn : pend[0];
-      pend[1] = npend == 1 ? nn : pend[1];
-      pend[2] = npend == 2 ? nn : pend[2];
-      pend[3] = npend == 3 ? nn : pend[3];
-      ++npend;
-      if (npend > lag) {
-        // the oldest of lag + 1 issued stages: its copies are waited for,
-        // then it is patched and signalled
-        if (!ws_signal<NB>(G, w, S, pend[0], lane)) {
-          stop = true;
-          break;
-        }
-        pend[0] = pend[1];
-        pend[1] = pend[2];
-        pend[2] = pend[3];
-        --npend;
-      }
+      const int li = (int)((nn >> 2) % (uint32_t)(S >> 2));
+      last[0] = li == 0 ? nn : last[0];
+      last[1] = li == 1 ? nn : last[1];
+      last[2] = li == 2 ? nn : last[2];
+      last[3] = li == 3 ? nn : last[3];
     }
     n += (uint32_t)nst;
     if (stop || row < 0) break;
     ++q;
   }
-  // the stages still outstanding are signalled; after a wait that ran out,
-  // their copies are only waited for
-  bool failed = false;
+  // whatever happened downstream, the copies this warp issued land before
+  // the block ends (a slot's phases complete in order: its last one is enough)
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-    if (i < npend) {
-      if (!failed) failed = !ws_signal<NB>(G, w, S, pend[i], lane);
-      if (failed)
-        ws_wait_copies(&w.tma[ws_slot(pend[i], S)], (pend[i] / (uint32_t)S) & 1u, kWsCopyDrainNs);
-    }
+    if (last[i] != ~0u)
+      ws_wait_copies(&w.tma[ws_slot(last[i], S)], (last[i] / (uint32_t)S) & 1u, kWsCopyDrainNs);
 }
 
 // ---------------------------------------------------------------- MMA --
+// The whole MMA warp waits for each stage's copies (and with them its
+// metadata and ratings), patches the ratings into their swizzled places,
+// makes them visible to the tensor cores, and lane 0 issues the products.
+// With `hold` (failure-path testing) the first row's accumulator is never
+// handed to the drain, whose bounded wait then runs out.
 template <int NB>
-__device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S, uint32_t tmem) {
+__device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S, uint32_t tmem,
+                                       int hold) {
+  const int lane = threadIdx.x & 31;
   const uint32_t idesc = idesc_bf16_mn(128, G.NP);
   const uint32_t base = smem_u32(w.stages);
   uint32_t n = 0;
   int q = 0;
   for (;;) {
     const int s = ws_slot(n, S);
-    if (!ws_wait(&w.full[s], (n / (uint32_t)S) & 1u, w.abort, w.wait_ns)) break;
-    tc_fence_after();
+    if (!ws_wait_warp(&w.tma[s], (n / (uint32_t)S) & 1u, w.abort, w.wait_ns)) break;
+    uint8_t* stage = w.stages + s * WsNb<NB>::kStageBytes;
+#pragma unroll
+    for (int t = 0; t < NB / 32; ++t)
+      ws_patch_rating<NB>(G, stage, w.rating[s * NB + lane + 32 * t], lane + 32 * t);
+    fence_proxy_async_smem();
+    __syncwarp();
     const StageMeta m = w.meta[s];
     const RowRec r = w.recs[m.rec];
     const int b = q & 1;
     if (m.flags & 1) {
-      if (!ws_wait(&w.acc_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, w.abort, w.wait_ns)) break;
-      tc_fence_after();
+      if (!ws_wait_warp(&w.acc_empty[b], ((uint32_t)(q >> 1) & 1u) ^ 1u, w.abort, w.wait_ns)) break;
     }
-    const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
-    if (m.cnt > 0) {
-      const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
-      // K-steps of 16 neighbours: two atoms apart; the leading byte offset
-      // steps between 64-feature blocks, the stride one between atoms
-      for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
-        const uint64_t dh = smem_desc_sw128(hi + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
-        const uint64_t dl = smem_desc_sw128(lo + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
-        tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
-        tc_mma_bf16(acc, dh, dl, idesc, 1u);
-        tc_mma_bf16(acc, dl, dh, idesc, 1u);
+    tc_fence_after();
+    if (lane == 0) {
+      const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
+      if (m.cnt > 0) {
+        const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
+        // K-steps of 16 neighbours: two atoms apart; the leading byte offset
+        // steps between 64-feature blocks, the stride one between atoms
+        for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
+          const uint64_t dh = smem_desc_sw128(hi + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
+          const uint64_t dl = smem_desc_sw128(lo + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
+          tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
+          tc_mma_bf16(acc, dh, dl, idesc, 1u);
+          tc_mma_bf16(acc, dl, dh, idesc, 1u);
+        }
       }
+      tc_commit(&w.empty[s]);
+      if ((m.flags & 2) && !(hold && q == 0)) tc_commit(&w.acc_full[b]);
     }
-    tc_commit(&w.empty[s]);
+    __syncwarp();
     ++n;
     if (m.flags & 2) {
-      tc_commit(&w.acc_full[b]);
       ++q;
       if (r.row < 0) break;
     }
   }
   // every MMA issued has completed before the tensor memory is freed
-  tc_commit(w.fin);
-  uint32_t polls = 0;
-  while (!mbar_try_wait_sleep(w.fin, 0, 20000u) && ++polls < kWsPolls) {
+  if (lane == 0) {
+    tc_commit(w.fin);
+    uint32_t polls = 0;
+    while (!mbar_try_wait_sleep(w.fin, 0, 20000u) && ++polls < kWsPolls) {
+    }
   }
+  __syncwarp();
 }
 
 __device__ __forceinline__ void ld8(const float* p, float (&x)[8]) {
@@ -851,9 +835,8 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&w.full[s], 32);  // the lanes of the warp that fills the stage
       mbar_init(&w.empty[s], 1);
-      mbar_init(&w.tma[s], 1);    // its lane 0's arrive with the bytes to expect
+      mbar_init(&w.tma[s], 1);  // lane 0 of the filling warp arrives with the bytes to expect
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&w.acc_full[b], 1);
@@ -892,7 +875,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   } else if (warp < 8) {
     ws_drain(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
-    if ((threadIdx.x & 31) == 0) ws_mma<NB>(G, w, S, tmem);
+    ws_mma<NB>(G, w, S, tmem, a.hold_arrive);
   } else if (ws_consumer_of(warp, C) >= 0) {
     ws_consume(a, G, w, C);
   }

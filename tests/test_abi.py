@@ -129,7 +129,7 @@ def test_struct_mirrors_match_the_c_layout(tmp_path, pyname, ctype):
     ("bpmf_set_graph", (1,)), ("bpmf_test_rmse", (None, None)),
     ("bpmf_get_state", (None, None, None, None, 0)), ("bpmf_get_thresholds", (0, None)),
     ("bpmf_get_sweep_info", (0, None, None)), ("bpmf_set_timing", (1,)),
-    ("bpmf_set_limits", (64, 0)),
+    ("bpmf_set_limits", (64, 0)), ("bpmf_set_test_hold", (1,)),
 ])
 def test_null_handle_is_rejected_with_a_message(libpath, name, args):
     """Every entry point that takes a handle checks it before anything else

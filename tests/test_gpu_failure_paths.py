@@ -59,11 +59,15 @@ def test_persistent_kernel_wait_timeout_is_reported_and_recovers(gpu_lib):
                   hub_min=1 << 30) as s:
         assert s.thresholds(0)[3] == 1  # the persistent kernel draws the rows
         s.set_state(U, V, hyper, it=3)
-        s.set_limits(wait_ns=1)
+        # the kernel withholds the first accumulator's hand-off: the drain's
+        # wait (bounded to 20 ms here) runs out and every role leaves
+        s.set_limits(wait_ns=20_000_000)
+        s.set_test_hold(1)
         with pytest.raises(bp.BpmfError) as e:
             s.sweep(0)
         assert e.value.code == bp.ECUDA
         assert "timed out" in bp.lib().bpmf_last_error().decode()
+        s.set_test_hold(0)
         s.set_limits(wait_ns=0)
         s.set_state(U, V, hyper, it=3)
         s.sweep(0)

@@ -2,16 +2,21 @@
 CPU under random interleavings.
 
 The roles are the kernel's: four gather warps (stage n by warp n % 4, ring
-slot (n % 4) + 4 ((n / 4) % (S / 4)), up to min(S / 4, 4) stages of a warp
-in flight, a stage signalled once a later one of the same warp has been
-issued), one MMA thread, the drain and the consumers, with the row hand-off
-through row_ready / row_read.  Barriers keep mbarrier semantics: a wait
-tells phases apart by parity only.  Every read is checked against what it
-must see (the stage's metadata, the row's record, the slot's row), and the
-run must end with every row consumed once, without a deadlock.  Two
-planted protocol mistakes must be caught: a drain that does not wait for a
-free consumer slot, and gather warps keeping one more stage in flight than
-the ring slots they own.
+slot (n % 4) + 4 ((n / 4) % (S / 4))) that wait for a free slot, write the
+stage's metadata, arrive on its transaction barrier with the bytes to
+expect and issue the copies; the copies, which land later (each fill as a
+process of its own); the MMA warp, which waits for a stage's transaction
+barrier (copies landed and metadata written), runs the products and frees
+the slot; the drain and the consumers, with the row hand-off through
+row_ready / row_read.  Barriers keep mbarrier semantics: a wait tells
+phases apart by parity only, and a transaction barrier's phase completes
+once its arrival is in and its expected bytes have landed.  Every read is
+checked against what it must see (the stage's metadata and data, the row's
+record, the slot's row); the gather warps wait for their last copies before
+they end; the run must end with every row consumed once, without a
+deadlock.  Two planted protocol mistakes must be caught: a drain that does
+not wait for a free consumer slot, and gather warps that refill a slot
+without waiting for it to be free.
 """
 import random
 
@@ -37,14 +42,44 @@ class Bar:
         return (self.phase & 1) != parity
 
 
+class TxBar:
+    """An mbarrier with one expected arrival per phase and a transaction count."""
+
+    def __init__(self):
+        self.pending = 1
+        self.tx = 0
+        self.phase = 0
+
+    def _check(self):
+        if self.pending == 0 and self.tx == 0:
+            self.phase += 1
+            self.pending = 1
+
+    def arrive_expect(self, nbytes):
+        self.tx += nbytes
+        self.pending -= 1
+        assert self.pending >= 0
+        self._check()
+
+    def complete_tx(self, nbytes):
+        self.tx -= nbytes
+        assert self.tx >= 0, "copy bytes landed that no arrival announced"
+        self._check()
+
+    def done(self, parity):
+        return (self.phase & 1) != parity
+
+
 def ws_slot(n, S):
     return (n & 3) + 4 * ((n >> 2) % (S >> 2))
 
 
 def run(S, C, rows, seed, slot=ws_slot, mistake=None):
     rnd = random.Random(seed)
-    full = [Bar(32) for _ in range(S)]
+    tma = [TxBar() for _ in range(S)]
     empty = [Bar(1) for _ in range(S)]
+    data = [None] * S  # stage whose copies last landed in each slot
+    copies = []
     acc_full, acc_empty = [Bar(1), Bar(1)], [Bar(128), Bar(128)]
     slot_full = [Bar(128) for _ in range(C)]
     slot_empty = [Bar(1) for _ in range(C)]
@@ -57,10 +92,14 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
     published = {}
     consumed = []
     errors = []
-    lag = min(S // 4 - 1, 3) + (1 if mistake == "lag_too_deep" else 0)
+    def copy(s, nn, nbytes):
+        for _ in range(rnd.randint(0, 6)):
+            yield
+        data[s] = nn
+        tma[s].complete_tx(nbytes)
 
     def gather(wg):
-        n, q, pend = 0, 0, []
+        n, q, last = 0, 0, {}
         while True:
             if wg == 0:
                 if q > 0:
@@ -73,39 +112,45 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
             qq, nst_row = published["row"]
             assert qq == q, ("row hand-off", qq, q)
             row_read.arrive(32)
-            last = nst_row is None
+            final = nst_row is None
             nst = max(1, nst_row or 0)
             st = (wg - (n & 3)) & 3
             while st < nst:
                 nn = n + st
                 s = slot(nn, S)
-                while not empty[s].done(((nn // S) & 1) ^ 1):
+                while mistake != "no_empty_wait" and not empty[s].done(((nn // S) & 1) ^ 1):
                     yield
                 if st == 0:
-                    recs[q % RECS] = ("sentinel" if last else "row", q)
+                    recs[q % RECS] = ("sentinel" if final else "row", q)
                 meta[s] = (q % RECS, st == 0, st == nst - 1, nn)
-                yield  # copies in flight
-                pend.append(nn)
-                if len(pend) > lag:
-                    full[slot(pend.pop(0), S)].arrive(32)
+                nbytes = rnd.choice([0, 512, 4096])  # a stage without ratings copies nothing
+                tma[s].arrive_expect(nbytes)
+                if nbytes:
+                    copies.append(copy(s, nn, nbytes))
+                else:
+                    data[s] = nn
+                last[s] = nn
                 st += 4
                 if rnd.random() < 0.5:
                     yield
             n += nst
-            if last:
+            if final:
                 break
             q += 1
-        for m in pend:
-            full[slot(m, S)].arrive(32)
+        # the copies issued land before the warp ends
+        for s, m in last.items():
+            while not tma[s].done((m // S) & 1):
+                yield
 
     def mma():
         n, q = 0, 0
         while True:
             s = slot(n, S)
-            while not full[s].done((n // S) & 1):
+            while not tma[s].done((n // S) & 1):
                 yield
             m = meta[s]
             assert m[3] == n, ("stage metadata", m, n)
+            assert data[s] == n, ("stage data", data[s], n)
             rec = recs[m[0]]
             b = q & 1
             if m[1]:
@@ -162,6 +207,8 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
     alive = [gather(w) for w in range(4)] + [mma(), drain()] + [consumer(c) for c in range(C)]
     steps = 0
     while alive and not errors:
+        alive.extend(copies)
+        copies.clear()
         a = rnd.choice(alive)
         try:
             next(a)
@@ -189,7 +236,7 @@ def test_protocol_under_random_interleavings(S, C):
         assert not errs, (S, C, seed, errs[:2])
 
 
-@pytest.mark.parametrize("mistake", ["no_slot_wait", "lag_too_deep"])
+@pytest.mark.parametrize("mistake", ["no_slot_wait", "no_empty_wait"])
 def test_planted_protocol_mistakes_are_caught(mistake):
     failures = sum(1 for seed in range(40) if run(8, 2, _rows(seed), seed, mistake=mistake))
     assert failures > 0
