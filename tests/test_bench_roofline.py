@@ -66,3 +66,23 @@ def test_netflix_users_figures():
     # the movies side has the same Gram work and far fewer factorisations
     g1, c1, _ = bench.algorithmic_work(ds, 100)[1]
     assert g1 == f_gram and c1 < f_chol / 20
+
+
+def test_relabel_by_degree_is_a_bijection_in_degree_order():
+    """bench.py --relabel degree: the same ratings, rows renumbered so that
+    degrees do not increase with the id; test rows renumbered alike."""
+    import numpy as np
+    import synth
+    ds = synth.powerlaw(300, 80, 4000, 8, 0.8, 0.5, seed=5)
+    rd = bench.relabel_by_degree(ds)
+    deg0 = np.bincount(ds.train_row, minlength=ds.M)
+    deg1 = np.bincount(rd.train_row, minlength=ds.M)
+    assert (np.diff(deg1) <= 0).all()
+    assert sorted(deg0) == sorted(deg1)
+    # one map takes old ids to new ones, for training and test rows alike
+    mp = {}
+    for a, b in zip(np.concatenate([ds.train_row, ds.test_row]),
+                    np.concatenate([rd.train_row, rd.test_row])):
+        assert mp.setdefault(int(a), int(b)) == int(b)
+    assert len(set(mp.values())) == len(mp)
+    assert np.array_equal(rd.train_col, ds.train_col) and np.array_equal(rd.train_val, ds.train_val)
