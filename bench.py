@@ -49,10 +49,10 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (2 flop each per cloc
 # full launch by ratings (the per-rating index and value reads dominate).
 TRAFFIC = {
     ("netflix", 0, 1, 6): (
-        (165.3e6 + 27.7e6) * 5,
+        852.59e6 + 183.91e6,
         "ncu dram__bytes_read + dram__bytes_write of the users launch with this schedule (six "
-        "consumers) on the 120,000 x 17,770 case with 18M training ratings, 193 MB, scaled x5 "
-        "by ratings to this launch (profiles/row_ws_powerlaw120k_k100.md)"),
+        "consumers), captured on this full-size workload (1-pass metrics; "
+        "profiles/dram_netflix_k100_fullsize.md)"),
 }
 
 
