@@ -98,7 +98,7 @@ typedef struct {
                            persistent warp-specialised kernel), 1 persistent kernel, 2 one CTA
                            per row with the Cholesky on tensor cores */
   int32_t autotune;   /* 1: bpmf_init times candidate thresholds for every automatic (-1)
-                         one on this GPU and keeps the fastest (paper Sec. IV-B sets its
+                         one on this GPU and keeps the fastest (paper Sec. III sets its
                          split threshold by hand); the choice is remembered for the process
                          per (device, K, path, side shape, degree histogram in powers of
                          two); 0: fixed defaults */
@@ -227,12 +227,12 @@ BPMF_API int bpmf_get_hyper_stats(bpmf_t *h, int side, double *xbar, double *S);
  * rating, one warp per row; light: degree <= light_max, FP32 Gram, one warp per row for
  * K <= 32, else one CTA per row; heavy: tensor-core Gram on the MIXED path,
  * FP32 CTA per row on BINNED; hub: degree >= hub_min, split across
- * CTAs) and the number of rows the last sweep redid in FP64 (paper Sec. IV-B:
+ * CTAs) and the number of rows the last sweep redid in FP64 (paper Sec. III:
  * a cheap kernel for rows with few ratings, split tasks for rows with many).
  * Errors: EINVAL. */
 BPMF_API int bpmf_get_sweep_info(bpmf_t *h, int side, int64_t bins[4], int64_t *fp64_rows);
 
-/* The schedule in effect for `side` (the degree bins of paper Sec. IV-B;
+/* The schedule in effect for `side` (the degree bins of paper Sec. III;
  * host output array): thresholds[0] = tiny_max (-1: no
  * rank-one bin), [1] = light_max, [2] = hub_min -- the configured values, the
  * defaults (tiny_max 0 on the BINNED and MIXED paths, light_max = tiny_max,
@@ -245,7 +245,7 @@ BPMF_API int bpmf_get_thresholds(bpmf_t *h, int side, int64_t thresholds[5]);
 /* Sets the schedule of `side` from five values in bpmf_get_thresholds' order
  * and meaning (host array, read only during the call), e.g. ones the
  * autotuner chose in an earlier process: rows are re-binned by degree (the
- * degree bins and hub splitting of paper Sec. IV-B) and the next step
+ * degree bins and hub splitting of paper Sec. III) and the next step
  * re-captures its graph.  tiny_max -1 .. 32, light_max >= -1, hub_min >= 1; the
  * kernel [3] must be one the path and K can run (what bpmf_get_thresholds
  * could report: 1 or 2 on the MIXED path where supported, else 0), the

@@ -27,7 +27,7 @@
 // one product of L_s^-1 with d + 1 vectors, one with L_s^-T, and O(d^2)
 // warp-wide scans -- instead of d K column steps, each a dependent square root
 // and division, of successive rank-one updates of the factor.  This is the
-// cheaper kernel for rows with few ratings of paper Sec. IV-B (Fig. 2).  The
+// cheaper kernel for rows with few ratings of paper Sec. III (Fig. 2).  The
 // factor's diagonal is L*_ii = (L_s)_ii prod_s M_s,ii, so the pivot rule of
 // the other row kernels (L*_ii^2 against Lambda*_ii) still decides which rows
 // go to the FP64 redo.

@@ -5,7 +5,7 @@
 //   Lambda* = Lambda_s + alpha sum_j v_j v_j^T,  b = Lambda_s mu_s + alpha sum_j r_ij v_j,
 //   L = chol(Lambda*),  u_i = L^-T (L^-1 b + z).
 // For K <= 32 a whole row fits one warp, so no block-wide barrier is needed
-// anywhere (the light-row kernel of the degree bins, paper Sec. IV-B):
+// anywhere (the light-row kernel of the degree bins, paper Sec. III):
 //   Gram: the neighbour rows are staged 32 at a time in the warp's shared
 //     memory with cp.async (double-buffered); lane l owns an RB x CB block of
 //     the KP x KP Gram (rows RB (l / 4) .., columns CB (l % 4) ..; KP = K
