@@ -62,28 +62,43 @@ __device__ __forceinline__ float comp(const float4& v, int e) {
 }
 
 // T = (L_s^-1)^T from the packed factor (row i at i (i + 1) / 2), one warp per
-// row k of T, i.e. column k of L_s^-1: L_s t = e_k by forward substitution in
-// FP64, each dot product split across the lanes.
+// row k of T, i.e. column k of L_s^-1: L_s t = e_k by column-oriented forward
+// substitution in FP64 -- lane l holds t_i for i = l + 32 m; at step j the
+// owner of row j scales t_j by 1 / L_jj (computed before the loop) and
+// broadcasts it, and every lane subtracts L_ij t_j from its rows i > j, so a
+// step is one shuffle and one multiply-add, with no reduction.
 __global__ void __launch_bounds__(32) linv_columns(const float* __restrict__ lchol, int K, int KP,
                                                    float* __restrict__ T) {
-  __shared__ double col[kMaxK];
+  constexpr int kMaxNpl = kMaxK / 32;
   const int k = blockIdx.x, lane = threadIdx.x, LD = KP + 1;
   float* out = T + (int64_t)k * LD;
-  for (int i = lane; i < LD; i += 32)
-    if (i < k || i >= K) out[i] = 0.f;
-  if (k >= K) return;
-  for (int i = k; i < K; ++i) {
-    const float* Li = lchol + tri(i);
-    double part = 0.0;
-    for (int q = k + lane; q < i; q += 32) part = fma((double)Li[q], col[q], part);
+  double t[kMaxNpl], rdiag[kMaxNpl];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-    const double v = ((i == k ? 1.0 : 0.0) - part) / (double)Li[i];
-    if (lane == 0) {
-      col[i] = v;
-      out[i] = (float)v;
+  for (int m = 0; m < kMaxNpl; ++m) {
+    const int i = lane + 32 * m;
+    t[m] = i == k ? 1.0 : 0.0;
+    rdiag[m] = i < K ? 1.0 / (double)lchol[tri(i) + i] : 0.0;
+  }
+  for (int j = k; j < K; ++j) {
+    const int owner = j & 31, mj = j >> 5;
+    double tj = 0.0;
+#pragma unroll
+    for (int m = 0; m < kMaxNpl; ++m)
+      if (m == mj) tj = t[m] * rdiag[m];
+    tj = __shfl_sync(kFull, tj, owner);
+#pragma unroll
+    for (int m = 0; m < kMaxNpl; ++m) {
+      const int i = lane + 32 * m;
+      if (i == j) t[m] = tj;
+      else if (i > j && i < K) t[m] = fma(-(double)lchol[tri(i) + j], tj, t[m]);
     }
-    __syncwarp();
+  }
+  for (int i = lane; i < LD; i += 32) {
+    double v = 0.0;
+#pragma unroll
+    for (int m = 0; m < kMaxNpl; ++m)
+      if (i == lane + 32 * m) v = t[m];
+    out[i] = i >= k && i < K ? (float)v : 0.f;
   }
 }
 
