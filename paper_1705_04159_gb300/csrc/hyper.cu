@@ -269,28 +269,38 @@ __device__ void cta_tri_inverse(const double* L, double* Linv, int K) {
 }
 
 // T = L^-1 for lower-triangular L (row-major, K x K, in global memory; rdiag
-// = 1 / L_ii), one warp per column (blockIdx.x = j): L t_j = e_j by forward
-// substitution,
-// each row's dot product split across the lanes and summed by shuffles.  The
-// columns are independent, so K CTAs run them side by side.
+// = 1 / L_ii), one warp per column (blockIdx.x = j): L t_j = e_j by
+// column-oriented forward substitution -- lane l holds the entries
+// l + 32 m; at step i the owner of row i scales it by rdiag[i] and
+// broadcasts it, and every lane subtracts L[r][i] t_i from its rows r > i.
+// The columns are independent, so K CTAs run them side by side.
 __global__ void __launch_bounds__(32) tri_inverse_cols(const double* __restrict__ L,
                                                        const double* __restrict__ rdiag, double* T,
                                                        int K, const double* ok) {
-  __shared__ double col[kMaxK];
+  constexpr int kNpl = kMaxK / 32;
   if (ok != nullptr && *ok == 0.0) return;
   const int j = blockIdx.x, lane = threadIdx.x;
-  for (int i = lane; i < j; i += 32) T[i * K + j] = 0.0;
-  for (int i = j; i < K; ++i) {
-    double part = 0.0;
-    for (int k = j + lane; k < i; k += 32) part = fma(L[i * K + k], col[k], part);
+  double t[kNpl];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    const double v = ((i == j ? 1.0 : 0.0) - part) * rdiag[i];
-    if (lane == 0) {
-      col[i] = v;
-      T[i * K + j] = v;
+  for (int m = 0; m < kNpl; ++m) t[m] = lane + 32 * m == j ? 1.0 : 0.0;
+  for (int i = j; i < K; ++i) {
+    const int mi = i >> 5;
+    double ti = 0.0;
+#pragma unroll
+    for (int m = 0; m < kNpl; ++m)
+      if (m == mi) ti = t[m] * rdiag[i];
+    ti = __shfl_sync(0xffffffffu, ti, i & 31);
+#pragma unroll
+    for (int m = 0; m < kNpl; ++m) {
+      const int r = lane + 32 * m;
+      if (r == i) t[m] = ti;
+      else if (r > i && r < K) t[m] = fma(-L[r * K + i], ti, t[m]);
     }
-    __syncwarp();
+  }
+#pragma unroll
+  for (int m = 0; m < kNpl; ++m) {
+    const int r = lane + 32 * m;
+    if (r < K) T[r * K + j] = r >= j ? t[m] : 0.0;
   }
 }
 
@@ -479,13 +489,32 @@ __global__ void __launch_bounds__(128) wishart_mu(HyperArgs a) {
     rd[k] = 1.0 / B[k * K + k];
   }
   __syncthreads();
-  for (int i = K - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) xs[i] = zr[i] * rd[i];
-    __syncthreads();
-    const double xi = xs[i];
-    for (int k = threadIdx.x; k < i; k += blockDim.x) zr[k] = fma(-B[i * K + k], xi, zr[k]);
-    __syncthreads();
+  // x = B^-T z from the bottom by warp 0, lane l holding z_k for
+  // k = l + 32 m: the owner of row i forms x_i and broadcasts it, every lane
+  // subtracts B[i][k] x_i from its rows k < i (each z_k sees the same updates
+  // in the same order as a serial back substitution)
+  if (threadIdx.x < 32) {
+    constexpr int kNpl = kMaxK / 32;
+    const int lane = threadIdx.x;
+    double z[kNpl];
+#pragma unroll
+    for (int m = 0; m < kNpl; ++m) z[m] = lane + 32 * m < K ? zr[lane + 32 * m] : 0.0;
+    for (int i = K - 1; i >= 0; --i) {
+      const int mi = i >> 5;
+      double xi = 0.0;
+#pragma unroll
+      for (int m = 0; m < kNpl; ++m)
+        if (m == mi) xi = z[m] * rd[i];
+      xi = __shfl_sync(0xffffffffu, xi, i & 31);
+      if (lane == (i & 31)) xs[i] = xi;
+#pragma unroll
+      for (int m = 0; m < kNpl; ++m) {
+        const int k = lane + 32 * m;
+        if (k < i) z[m] = fma(-B[i * K + k], xi, z[m]);
+      }
+    }
   }
+  __syncthreads();
   const double rb = 1.0 / sqrt(a.beta0 + (double)a.n);
   for (int k = threadIdx.x; k < K; k += blockDim.x) a.mu[k] = mus[k] + xs[k] * rb;
   __syncthreads();
