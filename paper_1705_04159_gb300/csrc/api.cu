@@ -51,6 +51,9 @@ void free_handle(Handle* h) {
   drop_graph(h);
   release_timers(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhi);
@@ -318,6 +321,13 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
             cudaSuccess) {
       set_error("bpmf_init: no CUDA device");
+      rc = BPMF_ECUDA;
+      break;
+    }
+    if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("bpmf_init: stream or event creation failed");
       rc = BPMF_ECUDA;
       break;
     }

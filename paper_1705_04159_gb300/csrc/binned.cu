@@ -31,23 +31,66 @@
 
 namespace gb {
 
+namespace {
+
+// The bins other than the hubs, in order, on stream st.
+int launch_other_bins(Handle* h, int s, const SweepArgs& a, cudaStream_t st);
+
+}  // namespace
+
+// The split hubs (their pieces, then the ordered sum and the factorisation)
+// write only the hub rows and their own partials, so they run as a second
+// branch beside the other bins: forked from the handle's stream, joined back
+// into it before the half-sweep ends (under graph capture the two branches
+// become parallel graph nodes).  A launch error on either branch still joins.
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   SideDev& sd = h->side[s];
   cudaStream_t st = h->stream;
   SweepArgs a = a0;
   a.rows = sd.perm;
   const bool tc = h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K);
+  const bool others = sd.n_hub < sd.R;
+  const bool fork = sd.n_hub > 0 && others && h->aux != nullptr;
+  cudaStream_t hs = fork ? h->aux : st;
+  int rc = BPMF_OK;
+  if (fork) {
+    BPMF_CUDA_CHECK(cudaEventRecord(h->ev_fork, st));
+    BPMF_CUDA_CHECK(cudaStreamWaitEvent(hs, h->ev_fork, 0));
+  }
+  if (sd.n_hub > 0) {
+    rc = tc ? launch_pieces_tc(a, sd.n_pieces, h->status, hs, &h->kernels)
+            : launch_pieces_fp32(a, sd.n_pieces, hs, &h->kernels);
+    if (rc == BPMF_OK) {
+      SweepArgs f = a;
+      f.row_begin = 0;
+      f.row_end = sd.n_hub;
+      rc = launch_hub_finish_fp32(f, hs, &h->kernels);
+    }
+  }
+  if (fork) {
+    const cudaError_t e1 = cudaEventRecord(h->ev_join, hs);
+    const int rc2 = rc == BPMF_OK ? launch_other_bins(h, s, a, st) : rc;
+    const cudaError_t e2 = cudaStreamWaitEvent(st, h->ev_join, 0);
+    if (rc2 != BPMF_OK) return rc2;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      set_error("launch_sweep_binned: branch join: %s",
+                cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+      return BPMF_ECUDA;
+    }
+    return BPMF_OK;
+  }
+  if (rc != BPMF_OK) return rc;
+  return launch_other_bins(h, s, a, st);
+}
+
+namespace {
+
+int launch_other_bins(Handle* h, int s, const SweepArgs& a, cudaStream_t st) {
+  SideDev& sd = h->side[s];
+  const bool tc = h->cfg.path == BPMF_PATH_MIXED && tc_supported(h->K);
   const int64_t e_hub = sd.n_hub;
   const int64_t e_heavy = e_hub + sd.bin_count[kBinHeavy];
   const int64_t e_light = e_heavy + sd.bin_count[kBinLight];
-  if (sd.n_hub > 0) {
-    if (tc) BPMF_TRY(launch_pieces_tc(a, sd.n_pieces, h->status, st, &h->kernels));
-    else BPMF_TRY(launch_pieces_fp32(a, sd.n_pieces, st, &h->kernels));
-    SweepArgs f = a;
-    f.row_begin = 0;
-    f.row_end = e_hub;
-    BPMF_TRY(launch_hub_finish_fp32(f, st, &h->kernels));
-  }
   SweepArgs r = a;
   if (tc || (h->cfg.path == BPMF_PATH_MIXED && ws_supported(h->K))) {
     r.row_begin = e_hub;
@@ -79,6 +122,8 @@ int launch_sweep_binned(Handle* h, int s, const SweepArgs& a0) {
   r.row_end = sd.R;
   return launch_rows_rank1(r, sd.lchol, sd.linvT, (int)sd.tiny_max, st, &h->kernels);
 }
+
+}  // namespace
 
 namespace {
 

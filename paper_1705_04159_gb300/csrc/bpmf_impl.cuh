@@ -116,6 +116,10 @@ struct Handle {
   bool use_graph = true;
   bool capturing = false;
   cudaStream_t cap_stream = nullptr;  // private stream the capture runs on
+  // second branch of a half-sweep: the split hubs run beside the other bins
+  // (forked from and joined back into the handle's stream by the two events)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_timing = false;          // timing state the graph was captured with
   int64_t graph_kernels = 0;          // kernels per replay
