@@ -495,15 +495,20 @@ def main():
     per = {k: ph[k] / max(1, pc[k]) for k in ph}
     dom = max(("rows_users", "rows_movies"), key=lambda k: per[k])
     side = 0 if dom == "rows_users" else 1
-    # the relevant bound of the mixed path: the slowest of the tensor-core
-    # Gram (bf16 peak), the FP32 Cholesky and solves (FP32 peak) and the
-    # algorithmic bytes (HBM); split-precision and padding work not counted
+    # the relevant bound: the slowest of the tensor-core Gram (bf16 peak), the
+    # FP32 Cholesky and solves (FP32 peak) and the algorithmic bytes (HBM) when
+    # most of the side's rows take a tensor-core kernel (heavy bin, kernel 1 or
+    # 2); otherwise Gram and factorisations on the FP32 lanes.  Split-precision
+    # and padding work not counted.
     peaks, peak_src = measured_peaks()
     f_gram, f_chol, nbytes = work[side]
     t_ms = per[dom]
     sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     fp32_peak, n_sms = fp32_peak_tflops(sm_mhz)
-    if args.path == "mixed":
+    bins = mixed["info"][side][0]
+    tensor_gram = (args.path == "mixed" and mixed["thresholds"][side][3] in (1, 2)
+                   and 2 * int(bins[2]) > int(sum(bins)))
+    if tensor_gram:
         # the Gram on the tensor cores (bf16), the factorisations on the FP32 lanes
         terms = {"tensor": f_gram / (peaks["bf16_tflops"] * 1e12) * 1e3,
                  "alu": f_chol / (fp32_peak * 1e12) * 1e3,
@@ -518,11 +523,12 @@ def main():
     elif bound == "tensor":
         achieved, peak, unit = f_gram / (t_ms / 1e3) / 1e12, peaks["bf16_tflops"], "TFLOP/s"
     else:
-        flops = f_chol if args.path == "mixed" else f_gram + f_chol
+        flops = f_chol if tensor_gram else f_gram + f_chol
         achieved, peak, unit = flops / (t_ms / 1e3) / 1e12, fp32_peak, "TFLOP/s"
     key = (args.workload, side, mixed["thresholds"][side][3], mixed["thresholds"][side][4])
     traffic, traffic_note = TRAFFIC.get(key, (None, "no ncu capture of this kernel version"))
-    roofline = {"kernel": f"row update, {'users' if side == 0 else 'movies'} side",
+    roofline = {"kernel": f"row update, {'users' if side == 0 else 'movies'} side"
+                          f" ({'tensor-core Gram' if tensor_gram else 'FP32 Gram'})",
                 "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                 "peak_note": (f"alu: FP32 CUDA-core peak from unit counts ({n_sms} SMs x "
