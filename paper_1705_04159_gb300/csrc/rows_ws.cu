@@ -921,7 +921,7 @@ bool ws_supported(int K) {
 // Stages (a multiple of 4, one or more ring slots per gather warp) and
 // consumer warps for latent dimension K and nb neighbours per stage.  With
 // `cons` > 0 that many consumers (as many as fit, if fewer) and the deepest
-// ring up to 16 stages that fits;
+// ring up to kWsMaxStages that fits;
 // otherwise 8 stages if at least 3 consumers fit beside them, else 4 stages
 // and as many consumers as fit.
 int ws_config(int K, int cons, int nb, int* S, int* C) {
@@ -940,7 +940,7 @@ int ws_config(int K, int cons, int nb, int* S, int* C) {
   int s = 8, c = 0;
   if (cons > 0) {
     c = std::min(cons, kWsMaxCons);
-    s = 16;
+    s = kWsMaxStages;
     while (s > 4 && ws_smem_bytes(G, s, c, nb) > max_smem) s -= 4;
     while (c > 1 && ws_smem_bytes(G, s, c, nb) > max_smem) --c;  // more than fit: cut
   } else {
