@@ -232,8 +232,11 @@ __host__ __device__ __forceinline__ uint32_t stream_word(uint32_t stream, int si
 // ------------------------------------------------------------ launchers --
 // structure.cu
 int build_structure(Handle* h, const int32_t* d_row, const int32_t* d_col, const float* d_val);
-int sort_pairs_u32(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_out,
-                   int32_t* vals_out, int64_t n, uint32_t max_key, cudaStream_t st);
+// stable LSD radix sort of (key, value) pairs by key into keys_out / vals_out;
+// keys_io / vals_io hold the input and serve as the other half of the
+// ping-pong pair (their contents are lost)
+int sort_pairs_u32(uint32_t* keys_io, int32_t* vals_io, uint32_t* keys_out, int32_t* vals_out,
+                   int64_t n, uint32_t max_key, cudaStream_t st);
 int order_rows_by_degree(Handle* h, int s);
 double device_mean(const float* d_val, int64_t n, double* d_red, cudaStream_t st, int* err);
 int sort_test_set(Handle* h, const int32_t* d_row, const int32_t* d_col, const float* d_val,

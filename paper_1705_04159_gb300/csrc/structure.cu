@@ -259,23 +259,17 @@ unsigned grid_for(int64_t n, int threads) {
 
 // Stable sort of (key, value) pairs by key, LSD with 8-bit digits; passes
 // stop once every key bit up to max_key has been consumed.
-int sort_pairs_u32(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* keys_out,
-                   int32_t* vals_out, int64_t n, uint32_t max_key, cudaStream_t st) {
+int sort_pairs_u32(uint32_t* keys_io, int32_t* vals_io, uint32_t* keys_out, int32_t* vals_out,
+                   int64_t n, uint32_t max_key, cudaStream_t st) {
   if (n <= 0) return BPMF_OK;
   int bits = 0;
   while (bits < 32 && (max_key >> bits) != 0u) ++bits;
   const int passes = bits == 0 ? 1 : (bits + 7) / 8;
   const int tiles = (int)((n + kSortTile - 1) / kSortTile);
-  uint32_t *ka = nullptr, *kb = nullptr;
-  int32_t *va = nullptr, *vb = nullptr, *counts = nullptr, *offs = nullptr;
-  BPMF_CUDA_CHECK(cudaMallocAsync(&ka, sizeof(uint32_t) * n, st));
-  BPMF_CUDA_CHECK(cudaMallocAsync(&kb, sizeof(uint32_t) * n, st));
-  BPMF_CUDA_CHECK(cudaMallocAsync(&va, sizeof(int32_t) * n, st));
-  BPMF_CUDA_CHECK(cudaMallocAsync(&vb, sizeof(int32_t) * n, st));
+  uint32_t *ka = keys_io, *kb = keys_out;
+  int32_t *va = vals_io, *vb = vals_out, *counts = nullptr, *offs = nullptr;
   BPMF_CUDA_CHECK(cudaMallocAsync(&counts, sizeof(int32_t) * (int64_t)kRadix * tiles, st));
   BPMF_CUDA_CHECK(cudaMallocAsync(&offs, sizeof(int32_t) * (int64_t)kRadix * tiles, st));
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(ka, keys_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(va, vals_in, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
   for (int p = 0; p < passes; ++p) {
     radix_hist<<<tiles, kSortThreads, 0, st>>>(ka, n, 8 * p, counts, tiles);
     BPMF_CUDA_CHECK(cudaGetLastError());
@@ -286,12 +280,11 @@ int sort_pairs_u32(const uint32_t* keys_in, const int32_t* vals_in, uint32_t* ke
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(keys_out, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
-  BPMF_CUDA_CHECK(cudaMemcpyAsync(vals_out, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
-  BPMF_CUDA_CHECK(cudaFreeAsync(ka, st));
-  BPMF_CUDA_CHECK(cudaFreeAsync(kb, st));
-  BPMF_CUDA_CHECK(cudaFreeAsync(va, st));
-  BPMF_CUDA_CHECK(cudaFreeAsync(vb, st));
+  // after an even number of passes the result is back in the input pair
+  if (ka != keys_out) {
+    BPMF_CUDA_CHECK(cudaMemcpyAsync(keys_out, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+    BPMF_CUDA_CHECK(cudaMemcpyAsync(vals_out, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+  }
   BPMF_CUDA_CHECK(cudaFreeAsync(counts, st));
   BPMF_CUDA_CHECK(cudaFreeAsync(offs, st));
   return BPMF_OK;
