@@ -487,7 +487,7 @@ int bpmf_set_test(bpmf_t* hh, int64_t n, const int32_t* row, const int32_t* col,
     // validate, then sort by user (stable) for gather locality
     rc = sort_test_set(h, d_row, d_col, d_val, n, keys, keys_sorted, ids, src);
     if (rc) break;
-    if (cudaMemsetAsync(h->tsum, 0, sizeof(double) * n, st) != cudaSuccess) {
+    if (cudaMemsetAsync(h->tsum, 0, sizeof(float2) * n, st) != cudaSuccess) {
       rc = BPMF_ECUDA;
       break;
     }

@@ -273,16 +273,24 @@ int set_thresholds(Handle* h, int s, const int64_t t[5]) {
 // candidate (hyperparameters drawn from the initial factors, output written
 // to scratch so that the sampler state is untouched), one threshold after the
 // other: hub_min, then light_max (MIXED path), then tiny_max.  The fastest
-// candidate stays.  Timings come from CUDA events around the sweep's launches.
+// candidate stays.  Timings come from CUDA events around the sweep's launches:
+// the least of `reps` timed runs after one warm-up run, and of more runs (up
+// to kTuneMaxReps) while the timed runs add up to less than kTuneMinMs, so
+// that short sweeps, whose single runs vary most, are timed as often as it
+// takes to compare them.
 namespace {
+
+constexpr int kTuneMaxReps = 8;
+constexpr float kTuneMinMs = 5.f;
 
 int time_sweep(Handle* h, int s, float* scratch, int reps, float* best_ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BPMF_CUDA_CHECK(cudaEventCreate(&e0));
   BPMF_CUDA_CHECK(cudaEventCreate(&e1));
   int rc = BPMF_OK;
-  float best = 3.0e38f;
-  for (int r = 0; r <= reps && rc == BPMF_OK; ++r) {  // the first run warms up
+  float best = 3.0e38f, total = 0.f;
+  for (int r = 0; rc == BPMF_OK; ++r) {  // the first run warms up
+    if (r > reps && (total >= kTuneMinMs || r > kTuneMaxReps)) break;
     SweepArgs a = make_sweep_args(h, s);
     a.X = scratch;
     if (cudaMemsetAsync(h->flag_count, 0, sizeof(int32_t), h->stream) != cudaSuccess ||
@@ -296,7 +304,10 @@ int time_sweep(Handle* h, int s, float* scratch, int reps, float* best_ms) {
     if (rc == BPMF_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = BPMF_ECUDA;
     float ms = 0.f;
     if (rc == BPMF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = BPMF_ECUDA;
-    if (rc == BPMF_OK && r > 0) best = std::min(best, ms);
+    if (rc == BPMF_OK && r > 0) {
+      best = std::min(best, ms);
+      total += ms;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -102,7 +102,7 @@ struct Handle {
   int32_t* trow = nullptr;
   int32_t* tcol = nullptr;
   float* tval = nullptr;
-  double* tsum = nullptr;    // running sum of predictions
+  float2* tsum = nullptr;    // running sum of predictions, (hi, lo) per pair
   double* terr = nullptr;    // [2] sample / mean squared error
   int64_t n_avg = 0;         // host mirror of *d_navg
   bool have_rmse = false;
