@@ -54,6 +54,9 @@ void free_handle(Handle* h) {
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->aux2) cudaStreamDestroy(h->aux2);
+  if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   for (int s = 0; s < 2; ++s) {
     SideDev& sd = h->side[s];
     dfree(sd.ptr); dfree(sd.idx); dfree(sd.val); dfree(sd.perm); dfree(sd.X); dfree(sd.Xhi);
@@ -61,7 +64,8 @@ void free_handle(Handle* h) {
     dfree(sd.lam); dfree(sd.mu); dfree(sd.lamaug); dfree(sd.lchol); dfree(sd.linvT); dfree(sd.xbar); dfree(sd.S);
     dfree(sd.piece_row); dfree(sd.piece_e0); dfree(sd.piece_e1); dfree(sd.hub_piece0);
   }
-  dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->status);
+  dfree(h->mu0); dfree(h->W0inv); dfree(h->red); dfree(h->wscr); dfree(h->red2); dfree(h->wscr2);
+  dfree(h->status);
   dfree(h->flag_rows); dfree(h->flag_count); dfree(h->trow); dfree(h->tcol); dfree(h->tval);
   dfree(h->tsum); dfree(h->terr); dfree(h->hub_part); dfree(h->d_iter); dfree(h->d_navg);
   dfree(h->ws_counter); dfree(h->ws_base);
@@ -139,16 +143,34 @@ int read_fp64_rows(Handle* h, int s) {
 
 // One Gibbs iteration (Algorithm 1): per side in the configured order the
 // hyperparameter draw then the row draws, then the test predictions, then
-// the iteration word advances.  Everything that changes from one iteration
-// to the next lives in device memory, so the same launches serve every
-// iteration.
+// the iteration word advances.  The second side's hyperparameter draw reads
+// only that side's factors, which the first side's draw and sweep leave
+// alone, so it runs on aux2 beside them (with its own scratch) and joins
+// before the second sweep: the one-CTA FP64 draws of the two sides overlap,
+// and the second side's reductions fill SMs the first side leaves idle.
+// Everything that changes from one iteration to the next lives in device
+// memory, so the same launches serve every iteration.
 int step_body(Handle* h) {
-  const int first = h->cfg.order == 0 ? BPMF_USERS : BPMF_MOVIES;
-  for (int q = 0; q < 2; ++q) {
-    const int s = q == 0 ? first : 1 - first;
-    BPMF_TRY(launch_hyper(h, s));
-    BPMF_TRY(sweep_one(h, s));
+  const int first = h->cfg.order == 0 ? BPMF_USERS : BPMF_MOVIES, second = 1 - first;
+  const bool fork = h->aux2 != nullptr;
+  int rc = BPMF_OK;
+  if (fork) {
+    BPMF_CUDA_CHECK(cudaEventRecord(h->ev_fork2, h->stream));
+    BPMF_CUDA_CHECK(cudaStreamWaitEvent(h->aux2, h->ev_fork2, 0));
+    rc = launch_hyper(h, second, h->aux2, true);
+    // the join is recorded and waited for whatever happened, so that a
+    // capture never ends with the branch unjoined
+    if (cudaEventRecord(h->ev_join2, h->aux2) != cudaSuccess && rc == BPMF_OK) rc = BPMF_ECUDA;
   }
+  if (rc == BPMF_OK) rc = launch_hyper(h, first);
+  if (rc == BPMF_OK) rc = sweep_one(h, first);
+  if (fork) {
+    if (cudaStreamWaitEvent(h->stream, h->ev_join2, 0) != cudaSuccess && rc == BPMF_OK) rc = BPMF_ECUDA;
+  } else if (rc == BPMF_OK) {
+    rc = launch_hyper(h, second);
+  }
+  if (rc != BPMF_OK) return rc;
+  BPMF_TRY(sweep_one(h, second));
   BPMF_TRY(launch_test_step(h));
   return launch_advance_iter(h);
 }
@@ -326,7 +348,10 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
     }
     if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
       set_error("bpmf_init: stream or event creation failed");
       rc = BPMF_ECUDA;
       break;
@@ -362,6 +387,8 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
                                     16LL * h->num_sms + 1024, 4096});
     if ((rc = dalloc(&h->red, h->red_len))) break;
     if ((rc = dalloc(&h->wscr, 6 * KK + 8 * K))) break;
+    if ((rc = dalloc(&h->red2, h->red_len))) break;
+    if ((rc = dalloc(&h->wscr2, 6 * KK + 8 * K))) break;
     if ((rc = dalloc(&h->mu0, K))) break;
     if ((rc = dalloc(&h->W0inv, KK))) break;
     if ((rc = dalloc(&h->status, 1))) break;
@@ -759,12 +786,13 @@ static cudaEvent_t take_event(Handle* h) {
   return e;
 }
 
-PhaseTimer::PhaseTimer(Handle* h_, int id_) : h(h_), id(id_) {
+PhaseTimer::PhaseTimer(Handle* h_, int id_, cudaStream_t st_)
+    : h(h_), id(id_), st(st_ ? st_ : h_->stream) {
   if (!h->timing) return;
   a = take_event(h);
   if (!a) return;
-  if (h->capturing) cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
-  else cudaEventRecord(a, h->stream);
+  if (h->capturing) cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+  else cudaEventRecord(a, st);
 }
 
 PhaseTimer::~PhaseTimer() {
@@ -774,8 +802,8 @@ PhaseTimer::~PhaseTimer() {
     h->event_pool.push_back(a);
     return;
   }
-  if (h->capturing) cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
-  else cudaEventRecord(b, h->stream);
+  if (h->capturing) cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+  else cudaEventRecord(b, st);
   h->pending.push_back({a, b, id});
 }
 

@@ -94,6 +94,11 @@ struct Handle {
   double* red = nullptr;    // reduction partials
   int64_t red_len = 0;
   double* wscr = nullptr;   // FP64 Wishart scratch (6 K*K + 8 K)
+  // a second set of both, for the hyperparameter draw of the side that runs
+  // second in an iteration: it runs on aux2 beside the first side's draw and
+  // sweep (it reads only its own side's factors, which neither changes)
+  double* red2 = nullptr;
+  double* wscr2 = nullptr;
   int* status = nullptr;    // device status word
   int32_t* flag_rows = nullptr;  // rows flagged for the FP64 redo (max R over sides)
   int32_t* flag_count = nullptr;
@@ -120,6 +125,8 @@ struct Handle {
   // (forked from and joined back into the handle's stream by the two events)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t aux2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool graph_timing = false;          // timing state the graph was captured with
   int64_t graph_kernels = 0;          // kernels per replay
@@ -149,7 +156,8 @@ struct PhaseTimer {
   Handle* h;
   int id;
   cudaEvent_t a = nullptr;
-  PhaseTimer(Handle* h_, int id_);
+  cudaStream_t st;
+  PhaseTimer(Handle* h_, int id_, cudaStream_t st_ = nullptr);
   ~PhaseTimer();
 };
 int resolve_timers(Handle* h);
@@ -247,7 +255,9 @@ int autotune_bins(Handle* h, int s, float* scratch);  // binned.cu
 int set_thresholds(Handle* h, int s, const int64_t t[5]);  // binned.cu
 
 // hyper.cu
-int launch_hyper(Handle* h, int s);
+// On stream st (the handle's stream if null) with the second scratch set if
+// alt (see Handle::red2).
+int launch_hyper(Handle* h, int s, cudaStream_t st = nullptr, bool alt = false);
 int launch_spd_inverse_f64(const double* A, double* Ainv, int K, double* scratch, int* status,
                            cudaStream_t st);
 int launch_check_spd_f64(const double* A, int K, double* scratch, int* status, float* lout,

@@ -827,18 +827,20 @@ int launch_colsum(const float* X, int64_t R, int K, double* part, int blocks, cu
 
 }  // namespace
 
-int launch_hyper(Handle* h, int s) {
+int launch_hyper(Handle* h, int s, cudaStream_t st, bool alt) {
   SideDev& sd = h->side[s];
   const int K = h->K;
-  cudaStream_t st = h->stream;
+  if (st == nullptr) st = h->stream;
+  double* red = alt ? h->red2 : h->red;
+  double* wscr = alt ? h->wscr2 : h->wscr;
   const int64_t R = sd.R;
   // blocks: up to 2 per SM, at least 64 rows each
   int blocks = 2 * h->num_sms;
   if ((int64_t)blocks * 64 > R) blocks = (int)std::max<int64_t>(1, (R + 63) / 64);
-  double* part = h->red;  // holds blocks * K * K doubles (sized at init)
-  float* xbarf = reinterpret_cast<float*>(h->wscr + 6 * K * K + 4 * K);
+  double* part = red;  // holds blocks * K * K doubles (sized at init)
+  float* xbarf = reinterpret_cast<float*>(wscr + 6 * K * K + 4 * K);
   {
-    PhaseTimer timer(h, BPMF_T_HYPER_REDUCE);
+    PhaseTimer timer(h, BPMF_T_HYPER_REDUCE, st);
     BPMF_TRY(launch_colsum(sd.X, R, K, part, blocks, st));
     colsum_final<<<(K + kFinalWarps - 1) / kFinalWarps, 32 * kFinalWarps, 0, st>>>(
         part, blocks, K, R, sd.xbar, xbarf);
@@ -860,7 +862,7 @@ int launch_hyper(Handle* h, int s) {
   a.tp = h->d_iter;
   a.side = s;
   a.K = K;
-  a.scr = h->wscr;
+  a.scr = wscr;
   a.lam = sd.lam;
   a.mu = sd.mu;
   a.lamaug = sd.lamaug;
@@ -868,7 +870,7 @@ int launch_hyper(Handle* h, int s) {
   a.status = h->status;
   a.gamma_cap = h->gamma_cap;
   {
-    PhaseTimer timer(h, BPMF_T_HYPER_DRAW);
+    PhaseTimer timer(h, BPMF_T_HYPER_DRAW, st);
     const int smem = wishart_factor_smem(K);
     BPMF_CUDA_CHECK(cudaFuncSetAttribute(wishart_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     wishart_factor<<<1, 512, smem, st>>>(a);

@@ -73,8 +73,8 @@ int64_t job_bytes(const Job& j, int num_sms) {
   b += 2 * j.nnz * 8;                               // idx + val, both sides
   b += (j.M + j.N) * (8 + 4 + 4 * K + 8);           // ptr, perm, X, bins
   b += 2 * (KK * 8 * 2 + (K + 1) * (K + 1) * 4 + KK * 4 + K * 16);
-  b += std::max<int64_t>(2LL * num_sms * KK, 16LL * num_sms + 1024) * 8;  // reduction partials
-  b += (6 * KK + 8 * K) * 8;                        // Wishart scratch
+  b += 2 * std::max<int64_t>(2LL * num_sms * KK, 16LL * num_sms + 1024) * 8;  // reduction partials (two sets)
+  b += 2 * (6 * KK + 8 * K) * 8;                    // Wishart scratch (two sets)
   b += std::max(j.M, j.N) * 4;                      // flagged rows
   b += j.n_test * (4 + 4 + 4 + 8);                  // test set and running sums
   b += (j.nnz / 2048 + 16) * (K + 8) * (K + 8) * 4; // split-row partial Grams
