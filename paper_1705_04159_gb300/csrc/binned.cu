@@ -272,8 +272,9 @@ int set_thresholds(Handle* h, int s, const int64_t t[5]) {
 // Each automatic threshold is chosen by timing one half-sweep of the side per
 // candidate (hyperparameters drawn from the initial factors, output written
 // to scratch so that the sampler state is untouched), one threshold after the
-// other: hub_min, then light_max (MIXED path), then tiny_max.  The fastest
-// candidate stays.  Timings come from CUDA events around the sweep's launches:
+// other: hub_min together with the persistent kernel's consumer count, then
+// light_max (MIXED path), then tiny_max, then the consumer count again.  The
+// fastest candidate stays.  Timings come from CUDA events around the sweep's launches:
 // the least of `reps` timed runs after one warm-up run, and of more runs (up
 // to kTuneMaxReps) while the timed runs add up to less than kTuneMinMs, so
 // that short sweeps, whose single runs vary most, are timed as often as it
@@ -388,38 +389,40 @@ int autotune_bins(Handle* h, int s, float* scratch) {
     BPMF_TRY(time_sweep(h, s, scratch, reps, &t_tc));
     sd.heavy_tc = t_tc < t_ws;
   }
-  if (!sd.heavy_tc && h->cfg.path == BPMF_PATH_MIXED && ws_supported(h->K) && sd.Xhi) {
-    // consumer warps of the persistent kernel: fewer leave room for a deeper
-    // stage ring (rows with many ratings), more factor more rows at once
-    int best_c = 0;
+  // the persistent kernel's consumer count and the hub threshold interact (a
+  // shape that suits long rows suits leaving the hubs whole), so they are
+  // searched together first (four consumer counts); the consumer count is
+  // refined once more at the end, with the bins fixed
+  const bool tune_cons = !sd.heavy_tc && h->cfg.path == BPMF_PATH_MIXED && ws_supported(h->K) && sd.Xhi;
+  const int64_t maxdeg = sd.deg_h.empty() ? 0 : sd.deg_h[0];
+  std::vector<int64_t> hubs;
+  if (h->cfg.hub_min < 0 && maxdeg >= 2048) {
+    for (int64_t v : {(int64_t)2048, (int64_t)4096, (int64_t)8192, (int64_t)16384, (int64_t)1 << 40})
+      if (v == (int64_t)1 << 40 || v <= maxdeg) hubs.push_back(v);
+  } else {
+    hubs.push_back(sd.hub_min);
+  }
+  if (hubs.size() > 1 || tune_cons) {
+    int64_t best_v = sd.hub_min;
+    int best_c = sd.ws_cons;
     float best = 3.0e38f;
-    for (int c : {0, 1, 2, 3, 4, 5, 6}) {
-      sd.ws_cons = c;
-      if (time_sweep(h, s, scratch, reps, &ms) != BPMF_OK) {
-        cudaGetLastError();  // that many consumers do not fit: not a candidate
-        continue;
-      }
-      if (ms < best) {
-        best = ms;
-        best_c = c;
+    for (int64_t v : hubs) {
+      BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, v));
+      for (int c : {0, 2, 4, 6}) {
+        if (!tune_cons && c != 0) break;
+        if (tune_cons) sd.ws_cons = c;
+        if (time_sweep(h, s, scratch, reps, &ms) != BPMF_OK) {
+          cudaGetLastError();  // that many consumers do not fit: not a candidate
+          continue;
+        }
+        if (ms < best) {
+          best = ms;
+          best_v = v;
+          best_c = tune_cons ? c : best_c;
+        }
       }
     }
     sd.ws_cons = best_c;
-  }
-  const int64_t maxdeg = sd.deg_h.empty() ? 0 : sd.deg_h[0];
-  if (h->cfg.hub_min < 0 && maxdeg >= 2048) {
-    int64_t best_v = sd.hub_min;
-    float best = 3.0e38f;
-    for (int64_t v : {(int64_t)2048, (int64_t)4096, (int64_t)8192, (int64_t)16384,
-                      (int64_t)1 << 40}) {
-      if (v != (int64_t)1 << 40 && v > maxdeg) continue;
-      BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, v));
-      BPMF_TRY(time_sweep(h, s, scratch, reps, &ms));
-      if (ms < best) {
-        best = ms;
-        best_v = v;
-      }
-    }
     BPMF_TRY(apply_bins(h, s, sd.tiny_max, sd.light_max, best_v));
   }
   const bool light_differs =
@@ -454,6 +457,25 @@ int autotune_bins(Handle* h, int s, float* scratch) {
       }
     }
     BPMF_TRY(apply_bins(h, s, best_v, std::max(light, best_v), sd.hub_min));
+  }
+  if (tune_cons) {
+    // consumer warps of the persistent kernel, once more with the bins fixed:
+    // fewer leave room for a deeper stage ring (rows with many ratings), more
+    // factor more rows at once
+    int best_c = sd.ws_cons;
+    float best = 3.0e38f;
+    for (int c : {0, 1, 2, 3, 4, 5, 6}) {
+      sd.ws_cons = c;
+      if (time_sweep(h, s, scratch, reps, &ms) != BPMF_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ms < best) {
+        best = ms;
+        best_c = c;
+      }
+    }
+    sd.ws_cons = best_c;
   }
   // the tuning draws left the side's hyperparameters set; the chain starts
   // without them, as before tuning
