@@ -13,8 +13,9 @@
 //     NB per stage (32, or 64 on a side whose rows average 256 or more
 //     ratings), by tensor-memory-accelerator gather4 copies (four neighbour
 //     rows x 64 features each) straight into MN-major operand tiles with the
-//     128-byte swizzle, into a ring of stages, and patches the rating in as
-//     feature K;
+//     128-byte swizzle, into a ring of stages (64-neighbour stages copy the
+//     features past 64 by 16-byte cp.async instead); the MMA warp patches
+//     the rating in as feature K;
 //   MMA (warp 8, one thread): per 16 neighbours hi.hi + hi.lo + lo.hi into
 //     one of two FP32 accumulators in tensor memory (G = X^T X with X the
 //     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped);
@@ -65,6 +66,12 @@ struct WsNb {
   static constexpr int kBlk = NB * 128;             // bytes of one 64-feature block
   static constexpr int kOpBytes = 2 * kBlk;         // 128 features (the MMA reads M = 128 rows)
   static constexpr int kStageBytes = 2 * kOpBytes;  // hi + lo
+  // Long-row stages split their copies: the first 64-feature block by TMA
+  // gather4, the rest by 16-byte cp.async through another request path, as
+  // the TMA issue rate (about 17 cycles per gather4 per SM) co-limits those
+  // sides; short-row sides keep every copy on the TMA, where cp.async's
+  // traffic through L1 would cost the consumers, which limit them.
+  static constexpr bool kSplitCopy = NB >= 64;
 };
 __host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 2 * nb * 128; }
 constexpr int kWsMaxStages = 16;
@@ -256,10 +263,12 @@ __device__ __forceinline__ uint32_t idesc_bf16_mn(int M, int N) {
 // by warp n % 4), so four stages are filled side by side.  In the warp that
 // fills stage n, lane l holds neighbours l, l + 32, .. (NB / 32 of them);
 // lane g < 4 ceil(cnt / 16) copies the rows of neighbours 4g .. 4g + 3 into
-// both operand tiles with one gather4 per 64-feature block and tile.  Rows
-// past cnt (up to the MMA's 16-neighbour step) are read at an out-of-range
-// row index, which the copy fills with zeros.  The rating (feature K) is
-// patched in once the copies have landed (ws_patch_rating).
+// both operand tiles with one gather4 per 64-feature block and tile (with
+// WsNb::kSplitCopy, the first block only: each lane copies the rest of its
+// neighbours' rows by cp.async).  Rows past cnt (up to the MMA's
+// 16-neighbour step) are read at an out-of-range row index, which the copy
+// fills with zeros.  The rating (feature K) is patched in once the copies
+// have landed (ws_patch_rating).
 __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int x, int y0,
                                             int y1, int y2, int y3, uint64_t* bar) {
   asm volatile(
@@ -268,6 +277,16 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3),
       "r"(smem_u32(bar))
       : "memory");
+}
+// 16-byte copy through L2 only, zero-filling past src_bytes (0: all zeros)
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+// the barrier counts one arrival of this thread once its earlier cp.async
+// copies have landed (the arrival is part of the barrier's initial count)
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
@@ -297,16 +316,45 @@ __device__ __forceinline__ void ws_issue_stage(const WsGeom& G, const SweepArgs&
   }
   // the arrive (release) publishes the lanes' metadata and rating writes with
   // the copies: the MMA warp waits for this barrier alone
+  const bool split = WsNb<NB>::kSplitCopy && nblk == 2;
+  const int ntma = split ? 1 : nblk;  // feature blocks copied by TMA
   __syncwarp();
-  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(ngroups * nblk * 2 * 512));
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(ngroups * ntma * 2 * 512));
   __syncwarp();
   if (lane < ngroups) {
     const uint32_t hi = smem_u32(stage) + (uint32_t)((lane >> 1) * kWsAtom + (lane & 1) * 512);
-    for (int b = 0; b < nblk; ++b) {
+    for (int b = 0; b < ntma; ++b) {
       const uint32_t off = (uint32_t)(b * WsNb<NB>::kBlk);
       tma_gather4(hi + off, map_hi, 64 * b, y[0], y[1], y[2], y[3], bar);
       tma_gather4(hi + WsNb<NB>::kOpBytes + off, map_lo, 64 * b, y[0], y[1], y[2], y[3], bar);
     }
+  }
+  if (split) {
+    // features 64 .. KA - 1 (chunks 0 .. c1 - 1 of the second block) by
+    // 16-byte cp.async into their swizzled places, rows past cnt (up to the
+    // MMA's 16-neighbour step) zero-filled; the later chunks stay zero from
+    // the start of the kernel.  Every lane arrives on the stage's barrier
+    // once its copies have landed.
+    const int c1 = (G.KA - 64 + 7) >> 3;
+    const int kmax = 16 * ((cnt + 15) >> 4);
+    const uint32_t base = smem_u32(stage) + (uint32_t)WsNb<NB>::kBlk;
+#pragma unroll
+    for (int u = 0; u < NB / 32; ++u) {
+      const int k = lane + 32 * u;
+      if (k < kmax) {
+        const bool live = k < cnt;
+        const int64_t jr = live ? (int64_t)j[u] : 0;
+        const __nv_bfloat16* h = a.Vhi + jr * a.KS + 64;
+        const __nv_bfloat16* l = a.Vlo + jr * a.KS + 64;
+        const uint32_t row = base + (uint32_t)((k >> 3) * kWsAtom + (k & 7) * 128);
+        for (int c = 0; c < c1; ++c) {
+          const uint32_t off = (uint32_t)((c ^ (k & 7)) << 4);
+          cp_async16_zfill(row + off, h + 8 * c, live ? 16u : 0u);
+          cp_async16_zfill(row + WsNb<NB>::kOpBytes + off, l + 8 * c, live ? 16u : 0u);
+        }
+      }
+    }
+    cp_async_arrive_noinc(bar);
   }
 }
 
@@ -836,7 +884,9 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&w.empty[s], 1);
-      mbar_init(&w.tma[s], 1);  // lane 0 of the filling warp arrives with the bytes to expect
+      // lane 0 of the filling warp arrives with the bytes to expect; with
+      // split copies, every lane once more after its cp.async copies
+      mbar_init(&w.tma[s], WsNb<NB>::kSplitCopy && G.KA > 64 ? 1 + 32 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&w.acc_full[b], 1);

@@ -14,9 +14,13 @@ once its arrival is in and its expected bytes have landed.  Every read is
 checked against what it must see (the stage's metadata and data, the row's
 record, the slot's row); the gather warps wait for their last copies before
 they end; the run must end with every row consumed once, without a
-deadlock.  Two planted protocol mistakes must be caught: a drain that does
-not wait for a free consumer slot, and gather warps that refill a slot
-without waiting for it to be free.
+deadlock.  With split copies (the long-row stages: the first feature block
+by TMA, the rest by cp.async), every lane of the filling warp also arrives on
+the stage's barrier once its own copies have landed, and the barrier counts
+those arrivals.  Three planted protocol mistakes must be caught: a drain that
+does not wait for a free consumer slot, gather warps that refill a slot
+without waiting for it to be free, and a split-copy barrier that does not
+count the lanes' arrivals.
 """
 import random
 
@@ -43,22 +47,28 @@ class Bar:
 
 
 class TxBar:
-    """An mbarrier with one expected arrival per phase and a transaction count."""
+    """An mbarrier with `count` expected arrivals per phase and a transaction count."""
 
-    def __init__(self):
-        self.pending = 1
+    def __init__(self, count=1):
+        self.count = count
+        self.pending = count
         self.tx = 0
         self.phase = 0
 
     def _check(self):
         if self.pending == 0 and self.tx == 0:
             self.phase += 1
-            self.pending = 1
+            self.pending = self.count
 
     def arrive_expect(self, nbytes):
         self.tx += nbytes
         self.pending -= 1
         assert self.pending >= 0
+        self._check()
+
+    def arrive(self):
+        self.pending -= 1
+        assert self.pending >= 0, "an arrival the barrier does not count"
         self._check()
 
     def complete_tx(self, nbytes):
@@ -74,9 +84,14 @@ def ws_slot(n, S):
     return (n & 3) + 4 * ((n >> 2) % (S >> 2))
 
 
-def run(S, C, rows, seed, slot=ws_slot, mistake=None):
+LANES = 4  # lanes of a filling warp in the model (the kernel's 32 arrive the same way)
+
+
+def run(S, C, rows, seed, slot=ws_slot, mistake=None, split=False):
     rnd = random.Random(seed)
-    tma = [TxBar() for _ in range(S)]
+    count = 1 + LANES if split and mistake != "split_count" else 1
+    tma = [TxBar(count) for _ in range(S)]
+    data_cp = [[None] * LANES for _ in range(S)]  # stage whose cp.async part each lane landed
     empty = [Bar(1) for _ in range(S)]
     data = [None] * S  # stage whose copies last landed in each slot
     copies = []
@@ -97,6 +112,14 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
             yield
         data[s] = nn
         tma[s].complete_tx(nbytes)
+
+    def cp_copy(s, nn, lane):
+        # a lane's cp.async copies (none for a stage without ratings) land,
+        # then its arrival on the stage's barrier
+        for _ in range(rnd.randint(0, 6)):
+            yield
+        data_cp[s][lane] = nn
+        tma[s].arrive()
 
     def gather(wg):
         n, q, last = 0, 0, {}
@@ -129,6 +152,9 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
                     copies.append(copy(s, nn, nbytes))
                 else:
                     data[s] = nn
+                if split:
+                    for lane in range(LANES):
+                        copies.append(cp_copy(s, nn, lane))
                 last[s] = nn
                 st += 4
                 if rnd.random() < 0.5:
@@ -151,6 +177,8 @@ def run(S, C, rows, seed, slot=ws_slot, mistake=None):
             m = meta[s]
             assert m[3] == n, ("stage metadata", m, n)
             assert data[s] == n, ("stage data", data[s], n)
+            if split:
+                assert all(d == n for d in data_cp[s]), ("stage cp.async data", data_cp[s], n)
             rec = recs[m[0]]
             b = q & 1
             if m[1]:
@@ -229,14 +257,16 @@ def _rows(seed):
     return [rnd.choice([0, 1, 1, 2, 3, 5, 9]) for _ in range(rnd.randint(1, 30))]
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("S,C", [(4, 6), (4, 1), (8, 2), (8, 3), (12, 1), (16, 2)])
-def test_protocol_under_random_interleavings(S, C):
+def test_protocol_under_random_interleavings(S, C, split):
     for seed in range(25):
-        errs = run(S, C, _rows(seed), seed)
+        errs = run(S, C, _rows(seed), seed, split=split)
         assert not errs, (S, C, seed, errs[:2])
 
 
-@pytest.mark.parametrize("mistake", ["no_slot_wait", "no_empty_wait"])
+@pytest.mark.parametrize("mistake", ["no_slot_wait", "no_empty_wait", "split_count"])
 def test_planted_protocol_mistakes_are_caught(mistake):
-    failures = sum(1 for seed in range(40) if run(8, 2, _rows(seed), seed, mistake=mistake))
+    failures = sum(1 for seed in range(40)
+                   if run(8, 2, _rows(seed), seed, mistake=mistake, split=mistake == "split_count"))
     assert failures > 0
