@@ -18,7 +18,9 @@
 //     the rating in as feature K;
 //   MMA (warp 8, one thread): per 16 neighbours hi.hi + hi.lo + lo.hi into
 //     one of two FP32 accumulators in tensor memory (G = X^T X with X the
-//     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped);
+//     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped); on
+//     64-neighbour stages hi.hi and hi.lo into two accumulators instead, and
+//     the drain adds hi.lo and its transpose (two products per step);
 //   drain (warps 4-7, thread m = tensor-memory lane m = matrix row m):
 //     forms A = base + alpha G (base = bordered [[Lambda_s, b0], [b0^T, 0]])
 //     and writes its lower triangle as 8 x 8 FP32 tiles into a free
@@ -72,6 +74,13 @@ struct WsNb {
   // sides; short-row sides keep every copy on the TMA, where cp.async's
   // traffic through L1 would cost the consumers, which limit them.
   static constexpr bool kSplitCopy = NB >= 64;
+  // Long-row stages also form the cross term h^T l + l^T h from one product:
+  // h^T h and h^T l go to two accumulators and the drain adds h^T l and its
+  // transpose (a second pass over the slot).  Two products per step instead
+  // of three; the drain has time to spare where rows are long, but not where
+  // they are short (the consumers wait for it there).
+  static constexpr bool kCrossOnce = NB >= 64;
+  static constexpr uint32_t kAccStride = kCrossOnce ? 256u : 128u;  // TMEM columns per buffer
 };
 __host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 2 * nb * 128; }
 constexpr int kWsMaxStages = 16;
@@ -151,6 +160,7 @@ struct WsShared {
   uint64_t* fin;
   uint64_t* row_ready;  // the gather leader published the next row
   uint64_t* row_read;   // every gather thread has read it
+  uint64_t* drain_sync;  // every drain thread has written its rows (cross-term pass)
   StageMeta* meta;
   RowRec* recs;
   float* rating;   // [stage][neighbour]: ratings waiting to be patched in
@@ -161,8 +171,8 @@ struct WsShared {
 };
 
 // mbarriers: empty and tma per stage, full and empty per accumulator, full
-// and empty per consumer slot, fin, row_ready, row_read (an even count, so
-// that what follows stays 16-byte aligned)
+// and empty per consumer slot, fin, row_ready, row_read, drain_sync (an even
+// count, so that what follows stays 16-byte aligned)
 __host__ __device__ inline int ws_nbar(int S, int C) { return (2 * S + 4 + 2 * C + 3 + 1) & ~1; }
 __host__ __device__ inline int ws_fixed_bytes(int nb, int S, int C) {
   // barriers, stage meta, row records, ratings, next_row, abort, taddr
@@ -192,6 +202,7 @@ __device__ __forceinline__ WsShared ws_carve(uint8_t* base, const WsGeom& G, int
   w.fin = w.slot_empty + C;
   w.row_ready = w.fin + 1;
   w.row_read = w.fin + 2;
+  w.drain_sync = w.fin + 3;
   p = reinterpret_cast<uint8_t*>(b + ws_nbar(S, C));
   w.meta = reinterpret_cast<StageMeta*>(p);
   w.recs = reinterpret_cast<RowRec*>(p + 16 * S);
@@ -521,7 +532,7 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
     }
     tc_fence_after();
     if (lane == 0) {
-      const uint32_t acc = tmem + (uint32_t)b * kWsAccCols;
+      const uint32_t acc = tmem + (uint32_t)b * WsNb<NB>::kAccStride;
       if (m.cnt > 0) {
         const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
         // K-steps of 16 neighbours: two atoms apart; the leading byte offset
@@ -529,9 +540,15 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
         for (int kk = 0; kk < (m.cnt + 15) / 16; ++kk) {
           const uint64_t dh = smem_desc_sw128(hi + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
           const uint64_t dl = smem_desc_sw128(lo + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
-          tc_mma_bf16(acc, dh, dh, idesc, ((m.flags & 1) && kk == 0) ? 0u : 1u);
-          tc_mma_bf16(acc, dh, dl, idesc, 1u);
-          tc_mma_bf16(acc, dl, dh, idesc, 1u);
+          const uint32_t first = ((m.flags & 1) && kk == 0) ? 0u : 1u;
+          if (WsNb<NB>::kCrossOnce) {
+            tc_mma_bf16(acc, dh, dh, idesc, first);
+            tc_mma_bf16(acc + kWsAccCols, dh, dl, idesc, first);
+          } else {
+            tc_mma_bf16(acc, dh, dh, idesc, first);
+            tc_mma_bf16(acc, dh, dl, idesc, 1u);
+            tc_mma_bf16(acc, dl, dh, idesc, 1u);
+          }
         }
       }
       tc_commit(&w.empty[s]);
@@ -595,6 +612,7 @@ __device__ __forceinline__ void ldg8(const float* p, float (&x)[8]) {
 
 // -------------------------------------------------------------- drain --
 // Thread m (0..127) owns tensor-memory lane m = row m of the accumulator.
+template <int NB>
 __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, const WsShared& w, int C,
                          uint32_t tmem) {
   const int m = threadIdx.x - kWsGather;
@@ -602,6 +620,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
   const int I = m >> 3, p = m & 7;
   const int slotf = G.slot_floats();
   int q = 0;
+  uint32_t nsync = 0;  // completed phases of drain_sync
   for (;;) {
     const int b = q & 1;
     if (!ws_wait_warp(&w.acc_full[b], (uint32_t)(q >> 1) & 1u, w.abort, w.wait_ns)) return;
@@ -623,7 +642,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
     float* slot = w.slots + c * slotf;
     float* tiles = slot + 4;
     float* diag0 = tiles + G.ntile * kWsTileF;
-    const uint32_t lane_base = tmem + (uint32_t)b * kWsAccCols + ((uint32_t)(32 * wq) << 16);
+    const uint32_t lane_base = tmem + (uint32_t)b * WsNb<NB>::kAccStride + ((uint32_t)(32 * wq) << 16);
     const bool gram = r.nst > 0;
     // columns 0 .. 32 wq + 31 cover the lower triangle of this warp's rows
     const int ncol = 32 * wq + 32 < G.NP ? 32 * wq + 32 : G.NP;
@@ -631,7 +650,15 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
       float v[16];
       if (gram) {
         tmem_ld16(lane_base + (uint32_t)c0, v);
-        tmem_wait_ld();
+        if (WsNb<NB>::kCrossOnce) {
+          float v2[16];
+          tmem_ld16(lane_base + kWsAccCols + (uint32_t)c0, v2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += v2[i];
+        } else {
+          tmem_wait_ld();
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -655,6 +682,34 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
             reinterpret_cast<float4*>(dst)[0] = make_float4(x[0], x[1], x[2], x[3]);
             reinterpret_cast<float4*>(dst)[1] = make_float4(x[4], x[5], x[6], x[7]);
             if (J == I && m < G.K) diag0[m] = dv;
+          }
+        }
+      }
+    }
+    if (WsNb<NB>::kCrossOnce && gram) {
+      // the transposed cross term: thread n adds alpha (h^T l)[n][j] to the
+      // slot's element (j, n) for j >= n (column n of the lower triangle,
+      // which only this thread touches here), after every drain thread has
+      // written its row above
+      // a bounded barrier wait, so that a drain warp that has left on a
+      // timeout cannot hold the others
+      mbar_arrive(w.drain_sync);
+      if (!ws_wait_warp(w.drain_sync, (uint32_t)nsync & 1u, w.abort, w.wait_ns)) return;
+      ++nsync;
+      const int n = m;
+      for (int c0 = (32 * wq) & ~15; c0 < G.NP; c0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + kWsAccCols + (uint32_t)c0, v);
+        tmem_wait_ld();
+        if (n < G.KA) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = c0 + i;
+            if (j >= n && j < G.KA) {
+              float* e = tiles + ((j >> 3) * ((j >> 3) + 1) / 2 + (n >> 3)) * kWsTileF + trow(j & 7) + (n & 7);
+              *e = fmaf(a.alpha, v[i], *e);
+              if (j == n && n < G.K) diag0[n] = *e;
+            }
           }
         }
       }
@@ -899,6 +954,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
     mbar_init(w.fin, 1);
     mbar_init(w.row_ready, 1);
     mbar_init(w.row_read, kWsGather);
+    mbar_init(w.drain_sync, kWsDrain);
     *w.abort = 0;
     mbar_fence_init();
   }
@@ -912,7 +968,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
     for (int e = threadIdx.x; e <= G.g; e += blockDim.x) w.sched[32 * G.nround + e] = (uint16_t)(rr[e] - r0);
   }
   if (warp == kWsMmaWarp) {
-    tmem_alloc(w.taddr, 2 * kWsAccCols);
+    tmem_alloc(w.taddr, 2 * WsNb<NB>::kAccStride);
     tmem_relinquish();
   }
   fence_proxy_async_smem();
@@ -923,7 +979,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   if (warp < 4) {
     ws_gather<NB>(a, G, w, S, counter, &map_hi, &map_lo);
   } else if (warp < 8) {
-    ws_drain(a, G, w, C, tmem);
+    ws_drain<NB>(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
     ws_mma<NB>(G, w, S, tmem, a.hold_arrive);
   } else if (ws_consumer_of(warp, C) >= 0) {
@@ -934,7 +990,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   if (*w.abort && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   if (warp == kWsMmaWarp) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * kWsAccCols);
+    tmem_dealloc(tmem, 2 * WsNb<NB>::kAccStride);
   }
 }
 
