@@ -49,7 +49,7 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (2 flop each per cloc
 # full launch by ratings (the per-rating index and value reads dominate).
 TRAFFIC = {
     ("netflix", 0, 1, 6): (
-        852.59e6 + 183.91e6,
+        849.56e6 + 183.31e6,
         "ncu dram__bytes_read + dram__bytes_write of the users launch with this schedule (six "
         "consumers), captured on this full-size workload (1-pass metrics; "
         "profiles/dram_netflix_k100_fullsize.md)"),
