@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(32 * kFinalWarps) colsum_final(
 constexpr int kScatThreads = 288;
 constexpr int kScatStages = 4;
 constexpr int kScatFlushRows = 1024;
-// rows per chunk: fewer for the 8 x 8 tiles, whose 64 accumulators keep
-// fewer subsets per tile
-__host__ __device__ constexpr int scat_rows(int TM) { return TM == 8 ? 16 : 32; }
+// rows per chunk (every tile size: the 8 x 8 tiles, whose 64 accumulators
+// leave fewer subsets per tile, measured 10% faster at 32 than at 16)
+__host__ __device__ constexpr int scat_rows(int) { return 32; }
 
 int scatter_tm(int K) { return K > 64 ? 8 : K > 16 ? 4 : K > 4 ? 2 : 1; }
 __host__ __device__ inline int scatter_tiles(int K, int TM) {
