@@ -75,6 +75,31 @@ def test_noalloc_stats_tall_matrix_at_the_largest_k(gpu_lib):
     assert np.max(np.abs(got_S - oS) / scale) <= 1e-5
 
 
+@pytest.mark.parametrize("K", [64, 63])
+def test_noalloc_stats_of_an_unaligned_view(gpu_lib, K):
+    """X one float past a 16-byte boundary (a view into a larger buffer): the
+    row copies take 4-byte pieces instead of 16-byte ones; the result is the
+    same statistics."""
+    import torch
+    bp = gpu_lib
+    R = 5003
+    rng = np.random.default_rng(41 + K)
+    U = (0.4 * rng.normal(size=(R, K)) - 0.1).astype(np.float32)
+    buf = torch.empty(R * K + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(U.ravel()).cuda()
+    X = buf[1:]
+    assert X.data_ptr() % 16 != 0
+    xbar = torch.full((K,), float("nan"), dtype=torch.float64, device="cuda")
+    S = torch.full((K * K,), float("nan"), dtype=torch.float64, device="cuda")
+    bp.bpmf_hyper_stats_noalloc(X, R, K, xbar, S)
+    torch.cuda.synchronize()
+    oxbar, oS = oracle.hyper_stats(U.astype(np.float64))
+    got_S = S.cpu().numpy().reshape(K, K)
+    assert np.max(np.abs(xbar.cpu().numpy() - oxbar)) <= 1e-6 * (np.abs(oxbar).max() + U.std())
+    scale = np.sqrt(np.outer(np.diag(oS), np.diag(oS)))
+    assert np.max(np.abs(got_S - oS) / scale) <= 1e-5
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits(gpu_lib):
     import torch
     bp = gpu_lib
