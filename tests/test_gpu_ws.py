@@ -25,7 +25,17 @@ CASES = {
     "long_k64": (lambda: synth.powerlaw(16000, 200, 200000, 64, 0.5, 0.9, seed=58), 64),
     "long_k127": (lambda: synth.powerlaw(9000, 150, 120000, 127, 0.5, 0.9, seed=59), 127),
     "long_k40": (lambda: synth.powerlaw(12000, 180, 150000, 40, 0.5, 0.9, seed=60), 40),
+    # the same with every tenth movie's ratings dropped: the long-row side
+    # then has rows without ratings (a stage with no neighbours, no Gram)
+    "long_k100_gaps": (lambda: _drop_cols(synth.powerlaw(24000, 300, 330000, 100, 0.5, 0.9,
+                                                          seed=61), 10), 100),
 }
+
+
+def _drop_cols(ds, every):
+    keep = ds.train_col % every != 0
+    ds.train_row, ds.train_col, ds.train_val = ds.train_row[keep], ds.train_col[keep], ds.train_val[keep]
+    return ds
 _cache = {}
 
 
