@@ -96,8 +96,8 @@ int launch_other_bins(Handle* h, int s, const SweepArgs& a, cudaStream_t st) {
     r.row_begin = e_hub;
     r.row_end = e_heavy;
     if (sd.Xhi && ws_supported(h->K) && !sd.heavy_tc)
-      BPMF_TRY(launch_rows_ws(r, h->num_sms, sd.ws_cons, sd.ws_nb, h->ws_counter, h->status, st,
-                              &h->kernels));
+      BPMF_TRY(launch_rows_ws(r, h->num_sms, sd.ws_cons, sd.ws_nb, sd.ws_cross, h->ws_counter,
+                              h->status, st, &h->kernels));
     else if (tc)
       BPMF_TRY(launch_rows_tc(r, h->status, st, &h->kernels));
     else
@@ -241,6 +241,7 @@ int setup_bins(Handle* h, int s) {
   sd.hub_min = 0;  // forces the pieces to be built
   sd.heavy_tc = h->cfg.heavy_kernel == 2 && tc_supported(h->K);
   sd.ws_nb = ws_stage_neighbours(R > 0 ? sd.ptr_h[R] : 0, R);
+  sd.ws_cross = sd.ws_nb == 64 && ws_cross_once(R > 0 ? sd.ptr_h[R] : 0, R);
   const int64_t tiny = h->cfg.tiny_max >= 0 ? h->cfg.tiny_max : default_tiny_max(h);
   const int64_t light = h->cfg.light_max >= 0 ? h->cfg.light_max : tiny;
   const int64_t hub = h->cfg.hub_min >= 0 ? h->cfg.hub_min : 2 * kPiece;

@@ -73,7 +73,8 @@ struct SideDev {
   int64_t max_deg = 0;
   bool heavy_tc = false;
   int ws_cons = 0;        // consumer warps of the persistent kernel (0: automatic)
-  int ws_nb = 32;         // neighbours per stage of the persistent kernel (32 or 64)  // heavy bin on the per-row tensor-core kernel instead of the persistent one
+  int ws_nb = 32;         // neighbours per stage of the persistent kernel (32 or 64)
+  bool ws_cross = false;  // its 64-neighbour stages form the hi/lo cross term from one product  // heavy bin on the per-row tensor-core kernel instead of the persistent one
   bool have_hyper = false;
   bool have_stats = false;
   int64_t fp64_rows = 0;

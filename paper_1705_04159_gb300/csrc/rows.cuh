@@ -62,11 +62,14 @@ int launch_pieces_tc(const SweepArgs& a, int64_t npieces, int* status, cudaStrea
 int launch_sweep_binned(Handle* h, int s, const SweepArgs& a);
 // heavy rows by the persistent warp-specialised kernel (rows_ws.cu)
 bool ws_supported(int K);
-// cons: consumer warps per CTA (0: automatic); nb: neighbours per stage (32 or 64)
-int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* counter, int* status,
-                   cudaStream_t st, int64_t* launches);
+// cons: consumer warps per CTA (0: automatic); nb: neighbours per stage (32 or 64);
+// cross: the cross term of the hi/lo split from one product (nb 64 only)
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, bool cross, int* counter,
+                   int* status, cudaStream_t st, int64_t* launches);
 // neighbours per stage of the persistent kernel for a side with nnz ratings over R rows
 int ws_stage_neighbours(int64_t nnz, int64_t R);
+// whether that side's 64-neighbour stages form the cross term from one product
+bool ws_cross_once(int64_t nnz, int64_t R);
 // rows row_begin..row_end, one warp per row, FP32 (rows_warp.cu); 1 <= K <= 32
 bool warp_supported(int K);
 int launch_rows_warp(const SweepArgs& a, cudaStream_t st, int64_t* launches);

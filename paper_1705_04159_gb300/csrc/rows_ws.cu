@@ -19,8 +19,9 @@
 //   MMA (warp 8, one thread): per 16 neighbours hi.hi + hi.lo + lo.hi into
 //     one of two FP32 accumulators in tensor memory (G = X^T X with X the
 //     stage's neighbours x features; lo.lo, ~2^-16 relative, is dropped); on
-//     64-neighbour stages hi.hi and hi.lo into two accumulators instead, and
-//     the drain adds hi.lo and its transpose (two products per step);
+//     sides whose rows average 2048 ratings or more, hi.hi and hi.lo into two
+//     accumulators instead, and the drain adds hi.lo and its transpose (two
+//     products per step);
 //   drain (warps 4-7, thread m = tensor-memory lane m = matrix row m):
 //     forms A = base + alpha G (base = bordered [[Lambda_s, b0], [b0^T, 0]])
 //     and writes its lower triangle as 8 x 8 FP32 tiles into a free
@@ -74,14 +75,17 @@ struct WsNb {
   // sides; short-row sides keep every copy on the TMA, where cp.async's
   // traffic through L1 would cost the consumers, which limit them.
   static constexpr bool kSplitCopy = NB >= 64;
-  // Long-row stages also form the cross term h^T l + l^T h from one product:
-  // h^T h and h^T l go to two accumulators and the drain adds h^T l and its
-  // transpose (a second pass over the slot).  Two products per step instead
-  // of three; the drain has time to spare where rows are long, but not where
-  // they are short (the consumers wait for it there).
-  static constexpr bool kCrossOnce = NB >= 64;
-  static constexpr uint32_t kAccStride = kCrossOnce ? 256u : 128u;  // TMEM columns per buffer
 };
+
+// With XO ("cross once") the cross term h^T l + l^T h comes from one product:
+// h^T h and h^T l go to two accumulators and the drain adds h^T l and its
+// transpose (a second pass over the slot).  Two products per step instead of
+// three, which pays where rows are long enough for the tensor pipe to set
+// the pace (sides averaging kWsCrossRow ratings or more); where they are
+// shorter the drain's second pass costs more than the product it saves.
+constexpr int64_t kWsCrossRow = 2048;
+template <bool XO>
+__host__ __device__ constexpr uint32_t ws_acc_stride() { return XO ? 256u : 128u; }  // TMEM columns per buffer
 __host__ __device__ constexpr int ws_stage_bytes(int nb) { return 2 * 2 * nb * 128; }
 constexpr int kWsMaxStages = 16;
 constexpr int kWsMaxCons = 7;
@@ -507,7 +511,7 @@ __device__ __forceinline__ void ws_gather(const SweepArgs& a, const WsGeom& G, c
 // makes them visible to the tensor cores, and lane 0 issues the products.
 // With `hold` (failure-path testing) the first row's accumulator is never
 // handed to the drain, whose bounded wait then runs out.
-template <int NB>
+template <int NB, bool XO>
 __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S, uint32_t tmem,
                                        int hold) {
   const int lane = threadIdx.x & 31;
@@ -532,7 +536,7 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
     }
     tc_fence_after();
     if (lane == 0) {
-      const uint32_t acc = tmem + (uint32_t)b * WsNb<NB>::kAccStride;
+      const uint32_t acc = tmem + (uint32_t)b * ws_acc_stride<XO>();
       if (m.cnt > 0) {
         const uint32_t hi = base + (uint32_t)s * WsNb<NB>::kStageBytes, lo = hi + WsNb<NB>::kOpBytes;
         // K-steps of 16 neighbours: two atoms apart; the leading byte offset
@@ -541,7 +545,7 @@ __device__ __forceinline__ void ws_mma(const WsGeom& G, const WsShared& w, int S
           const uint64_t dh = smem_desc_sw128(hi + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
           const uint64_t dl = smem_desc_sw128(lo + kk * 2 * kWsAtom, WsNb<NB>::kBlk, kWsAtom);
           const uint32_t first = ((m.flags & 1) && kk == 0) ? 0u : 1u;
-          if (WsNb<NB>::kCrossOnce) {
+          if (XO) {
             tc_mma_bf16(acc, dh, dh, idesc, first);
             tc_mma_bf16(acc + kWsAccCols, dh, dl, idesc, first);
           } else {
@@ -612,7 +616,7 @@ __device__ __forceinline__ void ldg8(const float* p, float (&x)[8]) {
 
 // -------------------------------------------------------------- drain --
 // Thread m (0..127) owns tensor-memory lane m = row m of the accumulator.
-template <int NB>
+template <bool XO>
 __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, const WsShared& w, int C,
                          uint32_t tmem) {
   const int m = threadIdx.x - kWsGather;
@@ -642,7 +646,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
     float* slot = w.slots + c * slotf;
     float* tiles = slot + 4;
     float* diag0 = tiles + G.ntile * kWsTileF;
-    const uint32_t lane_base = tmem + (uint32_t)b * WsNb<NB>::kAccStride + ((uint32_t)(32 * wq) << 16);
+    const uint32_t lane_base = tmem + (uint32_t)b * ws_acc_stride<XO>() + ((uint32_t)(32 * wq) << 16);
     const bool gram = r.nst > 0;
     // columns 0 .. 32 wq + 31 cover the lower triangle of this warp's rows
     const int ncol = 32 * wq + 32 < G.NP ? 32 * wq + 32 : G.NP;
@@ -650,7 +654,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
       float v[16];
       if (gram) {
         tmem_ld16(lane_base + (uint32_t)c0, v);
-        if (WsNb<NB>::kCrossOnce) {
+        if (XO) {
           float v2[16];
           tmem_ld16(lane_base + kWsAccCols + (uint32_t)c0, v2);
           tmem_wait_ld();
@@ -686,7 +690,7 @@ __device__ __forceinline__ void ws_drain(const SweepArgs& a, const WsGeom& G, co
         }
       }
     }
-    if (WsNb<NB>::kCrossOnce && gram) {
+    if (XO && gram) {
       // the transposed cross term: thread n adds alpha (h^T l)[n][j] to the
       // slot's element (j, n) for j >= n (column n of the lower triangle,
       // which only this thread touches here), after every drain thread has
@@ -925,7 +929,7 @@ __device__ __forceinline__ void ws_consume(const SweepArgs& a, const WsGeom& G, 
   }
 }
 
-template <int NB>
+template <int NB, bool XO>
 __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
                                                  const __grid_constant__ CUtensorMap map_hi,
                                                  const __grid_constant__ CUtensorMap map_lo, int S,
@@ -968,7 +972,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
     for (int e = threadIdx.x; e <= G.g; e += blockDim.x) w.sched[32 * G.nround + e] = (uint16_t)(rr[e] - r0);
   }
   if (warp == kWsMmaWarp) {
-    tmem_alloc(w.taddr, 2 * WsNb<NB>::kAccStride);
+    tmem_alloc(w.taddr, 2 * ws_acc_stride<XO>());
     tmem_relinquish();
   }
   fence_proxy_async_smem();
@@ -979,9 +983,9 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   if (warp < 4) {
     ws_gather<NB>(a, G, w, S, counter, &map_hi, &map_lo);
   } else if (warp < 8) {
-    ws_drain<NB>(a, G, w, C, tmem);
+    ws_drain<XO>(a, G, w, C, tmem);
   } else if (warp == kWsMmaWarp) {
-    ws_mma<NB>(G, w, S, tmem, a.hold_arrive);
+    ws_mma<NB, XO>(G, w, S, tmem, a.hold_arrive);
   } else if (ws_consumer_of(warp, C) >= 0) {
     ws_consume(a, G, w, C);
   }
@@ -990,7 +994,7 @@ __global__ void __launch_bounds__(512, 1) row_ws(const SweepArgs a,
   if (*w.abort && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
   if (warp == kWsMmaWarp) {
     tc_fence_after();
-    tmem_dealloc(tmem, 2 * WsNb<NB>::kAccStride);
+    tmem_dealloc(tmem, 2 * ws_acc_stride<XO>());
   }
 }
 
@@ -1018,6 +1022,8 @@ __global__ void refresh_shadow_kernel(const float* __restrict__ X, int64_t R, in
 int ws_stage_neighbours(int64_t nnz, int64_t R) {
   return R > 0 && nnz >= kWsLongRow * R ? 64 : 32;
 }
+
+bool ws_cross_once(int64_t nnz, int64_t R) { return R > 0 && nnz >= kWsCrossRow * R; }
 
 bool ws_supported(int K) {
   const int g = (K + 8) / 8;  // tiles per side of the bordered matrix
@@ -1107,16 +1113,17 @@ int encode_shadow_map(const __nv_bfloat16* p, int64_t rows, int KS, CUtensorMap*
 
 }  // namespace
 
-int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, int* counter, int* status,
-                   cudaStream_t st, int64_t* launches) {
+int launch_rows_ws(const SweepArgs& a, int num_sms, int cons, int nb, bool cross, int* counter,
+                   int* status, cudaStream_t st, int64_t* launches) {
   const int64_t nrows = a.row_end - a.row_begin;
   if (nrows <= 0) return BPMF_OK;
   if (nb != 32 && nb != 64) return BPMF_EINVAL;
+  if (cross && nb != 64) return BPMF_EINVAL;
   int S = 0, C = 0;
   BPMF_TRY(ws_config(a.K, cons, nb, &S, &C));
   const WsGeom G(a.K);
   const int smem = ws_smem_bytes(G, S, C, nb);
-  auto kern = nb == 64 ? row_ws<64> : row_ws<32>;
+  auto kern = nb == 32 ? row_ws<32, false> : cross ? row_ws<64, true> : row_ws<64, false>;
   BPMF_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   BPMF_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
   ws_base_kernel<<<1, 128, 0, st>>>(a, a.wsbase);

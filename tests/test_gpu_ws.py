@@ -18,13 +18,17 @@ CASES = {
     "k8": (lambda: synth.powerlaw(3000, 800, 40000, 8, 0.5, 0.9, seed=54), 8),
     "k33": (lambda: synth.powerlaw(4000, 900, 60000, 33, 0.5, 0.9, seed=55), 33),
     "k96": (lambda: synth.uniform(2500, 400, 50000, 96, seed=56), 96),
-    # movies averaging ~1000 ratings: that side's stages hold 64 neighbours,
-    # copy the features past 64 by cp.async and form the cross term from one
-    # product (two accumulators, the transpose added by the drain)
+    # movies averaging ~1000 ratings: that side's stages hold 64 neighbours
+    # and copy the features past 64 by cp.async
     "long_k100": (lambda: synth.powerlaw(24000, 300, 330000, 100, 0.5, 0.9, seed=57), 100),
     "long_k64": (lambda: synth.powerlaw(16000, 200, 200000, 64, 0.5, 0.9, seed=58), 64),
     "long_k127": (lambda: synth.powerlaw(9000, 150, 120000, 127, 0.5, 0.9, seed=59), 127),
     "long_k40": (lambda: synth.powerlaw(12000, 180, 150000, 40, 0.5, 0.9, seed=60), 40),
+    # movies averaging 2048 ratings or more: the cross term of the hi/lo split
+    # from one product (two accumulators, the transpose added by the drain)
+    "xlong_k100": (lambda: synth.powerlaw(60000, 100, 400000, 100, 0.5, 0.9, seed=62), 100),
+    "xlong_k64": (lambda: synth.powerlaw(40000, 80, 250000, 64, 0.5, 0.9, seed=63), 64),
+    "xlong_k40": (lambda: synth.powerlaw(30000, 60, 180000, 40, 0.5, 0.9, seed=64), 40),
     # the same with every tenth movie's ratings dropped: the long-row side
     # then has rows without ratings (a stage with no neighbours, no Gram)
     "long_k100_gaps": (lambda: _drop_cols(synth.powerlaw(24000, 300, 330000, 100, 0.5, 0.9,
@@ -102,7 +106,7 @@ def test_persistent_rows_chain_is_deterministic(gpu_lib):
 @pytest.mark.parametrize("name,cons", [("wide_k100", 1), ("wide_k100", 2), ("wide_k100", 6),
                                        ("k8", 1), ("k33", 2), ("k127", 1), ("long_k100", 1),
                                        ("long_k100", 3), ("long_k100", 7), ("long_k64", 2),
-                                       ("long_k127", 1)])
+                                       ("long_k127", 1), ("xlong_k100", 1), ("xlong_k100", 4)])
 def test_consumer_counts_and_ring_depths(gpu_lib, name, cons):
     """Fewer consumer warps leave room for a deeper stage ring (a gather warp
     then keeps up to four of its stages in flight); every such
