@@ -372,7 +372,7 @@ int bpmf_init(bpmf_t** out, int64_t M, int64_t N, int64_t nnz, const int32_t* ro
       if ((rc = dalloc(&sd.lchol, KK))) break;
       {
         const int64_t KP = (K + 31) & ~31;
-        if ((rc = dalloc(&sd.linvT, KP * (KP + 1)))) break;
+        if ((rc = dalloc(&sd.linvT, KP * (KP + 4)))) break;
       }
       if (cfg->path == BPMF_PATH_MIXED) {
         sd.KS = (K + 7) & ~7;

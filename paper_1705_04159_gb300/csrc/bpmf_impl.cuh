@@ -56,7 +56,7 @@ struct SideDev {
   double* mu = nullptr;    // K
   float* lamaug = nullptr; // (K+1)^2: Lambda_s bordered by b0 = Lambda_s mu_s (row and column K)
   float* lchol = nullptr;  // K(K+1)/2: chol(Lambda_s), lower, packed by rows, FP32 (rank-one kernel)
-  float* linvT = nullptr;  // KP x (KP + 1), KP = K rounded up to 32: (L_s^-1)^T (tiny-row kernel)
+  float* linvT = nullptr;  // KP x (KP + 4), KP = K rounded up to 32: (L_s^-1)^T (tiny-row kernel)
   // split rows (hubs): pieces of at most kPiece ratings, in degree order
   int64_t n_hub = 0, n_pieces = 0;
   int32_t* piece_row = nullptr;     // [n_pieces] row id

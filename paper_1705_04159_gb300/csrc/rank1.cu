@@ -33,12 +33,14 @@
 // go to the FP64 redo.
 //
 // Layout.  linv_columns writes T = (L_s^-1)^T, KP x LD floats (KP = K rounded
-// up to 32, LD = KP + 1, zero outside the triangle), once per sweep, in FP64
+// up to 32, LD = KP + 4, zero outside the triangle), once per sweep, in FP64
 // arithmetic from the packed FP32 factor.  Each CTA keeps T in shared memory;
 // its warps take rows in turn, one warp per row, lane l owning elements
 // l + 32 m.  T[k][i] at k LD + i: the forward product reads T[k][l + 32 m]
-// (consecutive in l) and the transposed one T[l + 32 m][k] (LD = 1 mod 32),
-// both free of bank conflicts.  Per warp: d + 1 vectors (x_t, then w_t and
+// (consecutive in l) one float at a time, and the transposed one reads
+// T[l + 32 m][k .. k + 3] as one 16-byte load (rows 16-byte aligned, LD = 4
+// mod 32, so eight lanes of a load phase fall on eight different groups of
+// four banks).  Per warp: d + 1 vectors (x_t, then w_t and
 // p_t; the last b, then c, then y), the d prefix sums B'_s (the backward pass
 // recomputes rho and gamma from them) and the normals z.
 #include <cuda_runtime.h>
@@ -70,7 +72,7 @@ __device__ __forceinline__ float comp(const float4& v, int e) {
 __global__ void __launch_bounds__(32) linv_columns(const float* __restrict__ lchol, int K, int KP,
                                                    float* __restrict__ T) {
   constexpr int kMaxNpl = kMaxK / 32;
-  const int k = blockIdx.x, lane = threadIdx.x, LD = KP + 1;
+  const int k = blockIdx.x, lane = threadIdx.x, LD = KP + 4;
   float* out = T + (int64_t)k * LD;
   double t[kMaxNpl], rdiag[kMaxNpl];
 #pragma unroll
@@ -158,7 +160,7 @@ __device__ __forceinline__ void scan_suffix(float (&v)[NPL], float (&ex)[NPL], i
 // Rows of block m need k < 32 (m + 1) only (L_s^-1 is lower triangular).
 template <int NPL, int G>
 __device__ __forceinline__ void lower_times(const float* T, float* v, int K, int lane) {
-  constexpr int KP = 32 * NPL, LD = KP + 1;
+  constexpr int KP = 32 * NPL, LD = KP + 4;
   float acc[G][NPL];
 #pragma unroll
   for (int g = 0; g < G; ++g)
@@ -248,7 +250,7 @@ template <int NPL>
 __global__ void __launch_bounds__(32 * kR1MaxWarps)
     row_rank1(const SweepArgs a, const float* __restrict__ lchol, const float* __restrict__ Tg,
               int D, int warps) {
-  constexpr int KP = 32 * NPL, LD = KP + 1;
+  constexpr int KP = 32 * NPL, LD = KP + 4;
   extern __shared__ __align__(16) float r1s[];
   const int K = a.K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -383,10 +385,13 @@ __global__ void __launch_bounds__(32 * kR1MaxWarps)
         if (k >= K) break;
         const float4 wv = *reinterpret_cast<const float4*>(zb + k);
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-#pragma unroll
-          for (int m = 0; m <= kc; ++m)
-            u[m] = fmaf(T[(lane + 32 * m) * LD + k + e], comp(wv, e), u[m]);
+        for (int m = 0; m <= kc; ++m) {
+          const float4 t4 = *reinterpret_cast<const float4*>(T + (lane + 32 * m) * LD + k);
+          u[m] = fmaf(t4.x, wv.x, u[m]);
+          u[m] = fmaf(t4.y, wv.y, u[m]);
+          u[m] = fmaf(t4.z, wv.z, u[m]);
+          u[m] = fmaf(t4.w, wv.w, u[m]);
+        }
       }
     }
     // pivot rule: L*_ii^2 = (L_s)_ii^2 / pr_i against pivot_rel Lambda*_ii
@@ -411,7 +416,7 @@ __global__ void __launch_bounds__(32 * kR1MaxWarps)
 
 template <int NPL>
 int launch_r1(const SweepArgs& a, const float* lchol, float* T, int D, cudaStream_t st) {
-  constexpr int KP = 32 * NPL, LD = KP + 1;
+  constexpr int KP = 32 * NPL, LD = KP + 4;
   linv_columns<<<KP, 32, 0, st>>>(lchol, a.K, KP, T);
   BPMF_CUDA_CHECK(cudaGetLastError());
   const size_t tbytes = sizeof(float) * KP * LD;

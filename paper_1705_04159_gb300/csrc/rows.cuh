@@ -75,7 +75,7 @@ bool warp_supported(int K);
 int launch_rows_warp(const SweepArgs& a, cudaStream_t st, int64_t* launches);
 // rows row_begin..row_end by rank-one updates of chol(Lambda_s) (rank1.cu)
 // rows of degree <= max_degree (<= kTinyDegreeMax) from chol(Lambda_s); linvT is
-// scratch of KP x (KP + 1) floats that the call fills with (L_s^-1)^T first
+// scratch of KP x (KP + 4) floats that the call fills with (L_s^-1)^T first
 int launch_rows_rank1(const SweepArgs& a, const float* lchol, float* linvT, int max_degree,
                       cudaStream_t st, int64_t* launches);
 

@@ -5,7 +5,7 @@ never forms Lambda* or its factor: with w_t = L_s^-1 x_t it builds the factor
 of I + sum_t w_t w_t^T as a product of d factors chol(I + p p^T), each
 diagonal plus semiseparable, whose inverse and inverse transpose act on a
 vector through one prefix or suffix sum.  The draw u = L*^-T (L*^-1 b + z)
-then takes two products with L_s^-1 (stored transposed, KP x KP + 1, zero
+then takes two products with L_s^-1 (stored transposed, KP x (KP + 4), zero
 outside the triangle, whole 32-row blocks skipped where it is zero) and warp
 scans over the lane layout l + 32 m.  These tests check:
   - the closed form of chol(I + p p^T) against numpy's Cholesky;
@@ -71,9 +71,10 @@ def factor(p, Bi=None, exclusive_by_subtraction=False):
 
 
 def linv_t(Ls, KP):
-    """T = (L_s^-1)^T, KP x (KP + 1), column by column by forward substitution."""
+    """T = (L_s^-1)^T, KP x (KP + 4) (the kernel's row stride; the last four
+    columns stay zero), column by column by forward substitution."""
     K = len(Ls)
-    T = np.zeros((KP, KP + 1))
+    T = np.zeros((KP, KP + 4))
     for k in range(K):
         col = np.zeros(K)
         for i in range(k, K):
